@@ -1,0 +1,511 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each uses a direct DFT, a closed
+form, an invariant, a physical limit stated in the paper, or brute force on a
+tiny input, so that a dropped term, a wrong sign or index, or a transposed
+operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+OM, BOX = 0.31, 320.0
+H0 = BOX / 2997.92458
+
+
+def rel(a, b):
+    a = np.asarray(a); b = np.asarray(b)
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(np.asarray(b).ravel()), 1e-300)
+
+
+def kt_of(nv, n):
+    return np.array([2.0 * n * math.sin(math.pi * m / n) for m in nv])
+
+
+def vertex_coords(n):
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    return x / n, y / n, z / n
+
+
+def mode_field(n, nv, phase=0.0):
+    x, y, z = vertex_coords(n)
+    return np.cos(2 * np.pi * (nv[0] * x + nv[1] * y + nv[2] * z) + phase)
+
+
+def lap7(f):
+    n = f.shape[0]
+    out = -6.0 * f
+    for ax in range(3):
+        out += np.roll(f, 1, axis=ax) + np.roll(f, -1, axis=ax)
+    return out * n * n
+
+
+# ---------------------------------------------------------------- FFT -------
+
+@pytest.mark.parametrize("n", [6, 8, 12])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft3d_matches_direct_dft(n, sign):
+    """Own FFT vs the O(N^6) DFT sum (radix 2, 3 and mixed)."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+    j = np.arange(n)
+    W = np.exp(sign * 2j * np.pi * np.outer(j, j) / n)
+    X = np.einsum("az,by,cx,zyx->abc", W, W, W, x, optimize=True)
+    assert np.max(np.abs(O.fft3d(x, sign) - X)) <= 1e-13 * np.max(np.abs(X))
+
+
+# ---------------------------------------------------------- background ------
+
+def test_tau_closed_form_matter_only():
+    """Omega_L = 0: tau = 2 sqrt(a) / H0 and a(tau) = (sqrt(a0) + H0 dtau / 2)^2."""
+    for a0, a1 in [(0.01, 0.02), (0.1, 1.0), (1 / 101, 1 / 100)]:
+        exact = 2.0 * (math.sqrt(a1) - math.sqrt(a0)) / H0
+        assert abs(O.tau_between(a0, a1, 1.0, H0) - exact) <= 1e-14 * exact
+        dt = 0.37 * exact
+        a_exact = (math.sqrt(a0) + 0.5 * H0 * dt) ** 2
+        assert abs(O.a_after(a0, dt, 1.0, H0) - a_exact) <= 1e-14 * a_exact
+
+
+def test_tau_lcdm_against_quadrature():
+    from scipy.integrate import quad
+    f = lambda a: 1.0 / (a * a * H0 * math.sqrt(OM / a ** 3 + 1 - OM))  # noqa: E731
+    for a0, a1 in [(1 / 101, 0.05), (0.3, 1.0)]:
+        ref = quad(f, a0, a1, epsabs=0, epsrel=2e-14, limit=200)[0]
+        assert abs(O.tau_between(a0, a1, OM, H0) - ref) <= 1e-13 * ref
+
+
+def test_schedule_geometric_and_half_steps():
+    a_n, dt, ah = O.schedule(100, 1 / 101, 1.0, OM, H0)
+    assert np.allclose(np.diff(np.log(a_n)), math.log(101) / 100, rtol=1e-13, atol=0)
+    total = O.tau_between(a_n[0], a_n[-1], OM, H0)
+    assert abs(dt.sum() - total) <= 1e-12 * total
+    assert np.all((ah > a_n[:-1]) & (ah < a_n[1:]))
+    # a_half sits at half the conformal time
+    for k in (0, 50, 99):
+        assert abs(O.tau_between(a_n[k], ah[k], OM, H0) - 0.5 * dt[k]) <= 1e-13 * dt[k]
+
+
+# ------------------------------------------------------------- CIC ----------
+
+def test_deposit_conserves_mass():
+    rng = np.random.default_rng(1)
+    n, npart = 16, 5000
+    pos = rng.random((npart, 3))
+    m = 0.31 / npart
+    rho = O.deposit_mass(n, pos, m)
+    assert abs(rho.sum() / n ** 3 - 0.31) <= 1e-13 * 0.31
+    assert rho.min() >= 0.0
+
+
+def test_single_particle_weights_brute_force():
+    """One particle at fractional offsets (1/4, 1/2, 3/4) of a cell next to the periodic edge."""
+    n = 8
+    pos = np.array([[(2 + 0.25) / n, (3 + 0.5) / n, (7 + 0.75) / n]])
+    rho = O.deposit_mass(n, pos, 1.0)
+    wx = {2: 0.75, 3: 0.25}; wy = {3: 0.5, 4: 0.5}; wz = {7: 0.25, 0: 0.75}
+    expect = np.zeros((n, n, n))
+    for ix, a in wx.items():
+        for iy, b in wy.items():
+            for iz, c in wz.items():
+                expect[iz, iy, ix] = a * b * c * n ** 3
+    assert np.max(np.abs(rho - expect)) <= 1e-12 * n ** 3
+
+
+def test_interpolation_reproduces_linear_field():
+    n = 8
+    rng = np.random.default_rng(2)
+    field = np.broadcast_to(np.arange(n, dtype=float)[None, None, :], (n, n, n)).copy()
+    pos = rng.random((100, 3)) * (n - 1) / n  # stay away from the periodic wrap in x
+    assert np.max(np.abs(O.cic_interp(field, pos) - pos[:, 0] * n)) <= 1e-12
+
+
+def test_two_particles_interpolation_brute_force():
+    n = 8
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((n, n, n))
+    pos = np.array([[0.99, 0.01, 0.5], [0.3, 0.7, 0.93]])
+    got = O.cic_interp(f, pos)
+    for p, g in zip(pos, got):
+        s = p * n
+        i = np.floor(s).astype(int); fr = s - i
+        v = 0.0
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    w = (fr[0] if dx else 1 - fr[0]) * (fr[1] if dy else 1 - fr[1]) * (fr[2] if dz else 1 - fr[2])
+                    v += w * f[(i[2] + dz) % n, (i[1] + dy) % n, (i[0] + dx) % n]
+        assert abs(g - v) <= 1e-14
+
+
+def test_centred_gradient_of_sine():
+    n = 16
+    x, y, z = vertex_coords(n)
+    f = np.sin(2 * np.pi * (x + 2 * y))
+    g0 = O.gradient(f, 0); g1 = O.gradient(f, 1); g2 = O.gradient(f, 2)
+    c = np.cos(2 * np.pi * (x + 2 * y))
+    assert np.max(np.abs(g0 - c * math.sin(2 * np.pi / n) * n)) <= 1e-12
+    assert np.max(np.abs(g1 - c * math.sin(4 * np.pi / n) * n)) <= 1e-12
+    assert np.max(np.abs(g2)) <= 1e-12
+
+
+# -------------------------------------------------------- stress-energy -----
+
+def test_projection_rest_particles_uniform_potential():
+    """u = 0, phi = c, chi = d: only T^00 survives and carries the (1 + 3 phi) volume factor (Eq. Newtondens)."""
+    n, npart, a, c, d = 8, 300, 0.02, 1e-3, 4e-4
+    pos = np.random.default_rng(4).random((npart, 3))
+    mom = np.zeros((npart, 3)); m = 0.31 / npart
+    s00, s0i, sij = O.project(n, pos, mom, m, a, np.full((n, n, n), c), np.full((n, n, n), d))
+    assert abs(s00.sum() / n ** 3 - a * 0.31 * (1 + 3 * c)) <= 1e-13
+    assert np.max(np.abs(s0i)) == 0.0 and np.max(np.abs(sij)) == 0.0
+
+
+def test_projection_momentum_density_and_dust_stress():
+    n, npart, a = 8, 300, 0.02
+    rng = np.random.default_rng(5)
+    pos = rng.random((npart, 3)); mom = rng.standard_normal((npart, 3)) * 1e-3; m = 0.31 / npart
+    c, d = 2e-4, 5e-5
+    s00, s0i, sij = O.project(n, pos, mom, m, a, np.full((n, n, n), c), np.full((n, n, n), d))
+    assert rel(s0i.reshape(3, -1).sum(1) / n ** 3, (1 + 4 * c - d) * m * mom.sum(0)) <= 1e-13
+    # zero potential: T_ij = sum m u_i u_j / E  (dust), symmetric ordering xx,xy,xz,yy,yz,zz
+    s00, s0i, sij = O.project(n, pos, mom, m, a, np.zeros((n, n, n)), np.zeros((n, n, n)))
+    E = np.sqrt(a * a + (mom ** 2).sum(1))
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for k, (i, j) in enumerate(pairs):
+        assert abs(sij[k].sum() / n ** 3 - (m * mom[:, i] * mom[:, j] / E).sum()) <= 1e-13 * abs(
+            (m * mom[:, i] * mom[:, j] / E).sum()) + 1e-30
+    assert abs(s00.sum() / n ** 3 - (m * E).sum()) <= 1e-13 * (m * E).sum()
+
+
+def test_projection_ultrarelativistic_equation_of_state():
+    """u >> a: the trace of T_ij approaches T^00 (pressure = energy density / 3)."""
+    n, npart, a = 8, 200, 1e-3
+    rng = np.random.default_rng(6)
+    pos = rng.random((npart, 3)); mom = rng.standard_normal((npart, 3)); m = 1.0 / npart
+    z = np.zeros((n, n, n))
+    s00, _, sij = O.project(n, pos, mom, m, a, z, z)
+    trace = sij[0] + sij[3] + sij[5]
+    assert rel(trace, s00) <= 1e-4
+
+
+# ------------------------------------------------------------- solves -------
+
+def test_single_mode_phi_closed_form():
+    n, A = 16, 0.7
+    nv = (1, -2, 3)
+    a, hc, dtp = 0.05, 0.3, 0.02
+    cphi = 3 * hc / dtp + 3 * hc * hc
+    R = A * mode_field(n, nv)
+    phi, chi, B, _ = O.solve_sources(n, R, a=a, hc=hc, dtau_prev=dtp)
+    k2 = (kt_of(nv, n) ** 2).sum()
+    assert np.max(np.abs(phi + R / (k2 + cphi))) <= 1e-14 * A
+    assert np.max(np.abs(chi)) == 0.0 or np.max(np.abs(chi)) <= 1e-30
+
+
+def test_phi_discrete_residual():
+    """(7-point Laplacian - c) phi reproduces R in configuration space, mean mode included."""
+    n = 12
+    R = np.random.default_rng(7).standard_normal((n, n, n)) + 0.3
+    hc, dtp = 0.25, 0.05
+    cphi = 3 * hc / dtp + 3 * hc * hc
+    phi, *_ = O.solve_sources(n, R, hc=hc, dtau_prev=dtp)
+    assert rel(lap7(phi) - cphi * phi, R) <= 1e-13
+
+
+def test_newtonian_poisson_residual():
+    n = 12
+    R = np.random.default_rng(8).standard_normal((n, n, n))
+    R -= R.mean()
+    phi, chi, B, _ = O.solve_sources(n, R, newtonian=True)
+    assert rel(lap7(phi), R) <= 1e-13
+    assert abs(phi.mean()) <= 1e-15
+
+
+def _sig_from_tensor(T, f):
+    """Sig (xx,xy,xz,yy,yz,zz) = T_ij * f."""
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    return np.stack([T[i, j] * f for i, j in pairs])
+
+
+def test_chi_from_pure_scalar_source_is_half():
+    """Sig_ij = (D_i D_j - delta_ij Lap/3) f  =>  chi = f/2 (scalar sector of Eq. spacespace)."""
+    n = 16
+    nv = (2, 1, -3)
+    kt = kt_of(nv, n)
+    f = 1e-3 * mode_field(n, nv, 0.4)
+    T = -np.outer(kt, kt) + np.eye(3) * (kt @ kt) / 3.0
+    phi, chi, B, ts = O.solve_sources(n, np.zeros((n, n, n)), np.zeros((3, n, n, n)), _sig_from_tensor(T, f),
+                                      dtau=0.01, hc=0.1, hc_half=0.1)
+    assert rel(chi, f / 2) <= 1e-13
+    assert np.max(np.abs(B)) <= 1e-18
+    assert np.max(np.abs(ts)) <= 1e-12 * np.max(np.abs(np.fft.fftn(f)))  # no spin-2 part
+
+
+def test_tt_source_gives_no_chi_and_drives_only_its_helicity():
+    n = 16
+    nv = (1, 2, 2)
+    kt = kt_of(nv, n)
+    ep, ex = O.polarisations_kt(nv, kt)
+    f = mode_field(n, nv)
+    phi, chi, B, ts = O.solve_sources(n, np.zeros((n, n, n)), None, _sig_from_tensor(ep, f), dtau=0.01,
+                                      hc=0.1, hc_half=0.1)
+    assert np.max(np.abs(chi)) <= 1e-15
+    hp, hx = ts[0], ts[1]
+    assert np.max(np.abs(hp)) > 0
+    assert np.max(np.abs(hx)) <= 1e-12 * np.max(np.abs(hp))
+
+
+def test_tensor_relaxes_to_static_solution():
+    """Constant TT source with Hubble friction: h+ -> s / ktilde^2 (static limit of Eq. spacespace)."""
+    n = 8
+    nv = (1, 0, 2)
+    kt = kt_of(nv, n)
+    k2 = kt @ kt
+    ep, _ = O.polarisations_kt(nv, kt)
+    f = mode_field(n, nv)
+    Sig = _sig_from_tensor(ep, f)
+    ts = None
+    for _ in range(400):
+        *_, ts = O.solve_sources(n, np.zeros((n, n, n)), None, Sig, dtau=0.05, hc=2.0, hc_half=2.0, tensor=ts)
+    # the mode nv carries |Sig_k| = N^3/2 with e+ normalised to e+_ij e+_ij = 1
+    idx = (nv[2] % n, nv[1] % n, nv[0] % n)
+    assert abs(ts[0][idx] - (n ** 3 / 2) / k2) <= 1e-9 * (n ** 3 / 2) / k2
+
+
+def test_longitudinal_momentum_gives_no_frame_dragging():
+    n = 16
+    nv = (1, 3, -2)
+    kt = kt_of(nv, n)
+    f = mode_field(n, nv, 0.3)
+    F = np.stack([kt[i] * f for i in range(3)])
+    phi, chi, B, _ = O.solve_sources(n, np.zeros((n, n, n)), F, None, dtau=0.01)
+    assert np.max(np.abs(B)) <= 1e-15 * np.max(np.abs(F))
+
+
+def test_transverse_momentum_mode_closed_form():
+    """-1/4 Lap B = P F: a transverse single mode F = e cos(k.x) gives B = 4 e cos(k.x) / ktilde^2."""
+    n = 16
+    nv = (2, -1, 1)
+    kt = kt_of(nv, n)
+    e = np.cross(kt, [1.0, 0.0, 0.0]); e /= np.linalg.norm(e)
+    f = mode_field(n, nv)
+    F = np.stack([e[i] * f for i in range(3)])
+    phi, chi, B, _ = O.solve_sources(n, np.zeros((n, n, n)), F, None, dtau=0.01)
+    expect = np.stack([4 * e[i] * f / (kt @ kt) for i in range(3)])
+    assert rel(B, expect) <= 1e-13
+
+
+@pytest.mark.parametrize("nv", [(1, 0, 0), (0, 3, 0), (1, 1, 0), (2, -1, 3), (-3, 2, 2), (1, 1, 1)])
+def test_polarisation_tensors_are_tt_orthonormal_and_complete(nv):
+    n = 8
+    kt = kt_of(nv, n)
+    ep, ex = O.polarisations_kt(nv, kt)
+    kh = kt / np.linalg.norm(kt)
+    for e in (ep, ex):
+        assert abs(np.trace(e)) <= 1e-15
+        assert np.max(np.abs(e @ kh)) <= 1e-15
+        assert np.max(np.abs(e - e.T)) <= 1e-15
+        assert abs((e * e).sum() - 1.0) <= 1e-15
+    assert abs((ep * ex).sum()) <= 1e-15
+    P = np.eye(3) - np.outer(kh, kh)
+    lam = 0.5 * (np.einsum("ik,jl->ijkl", P, P) + np.einsum("il,jk->ijkl", P, P)) - 0.5 * np.einsum(
+        "ij,kl->ijkl", P, P)
+    comp = np.einsum("ij,kl->ijkl", ep, ep) + np.einsum("ij,kl->ijkl", ex, ex)
+    assert np.max(np.abs(comp - lam)) <= 1e-14
+
+
+# -------------------------------------------------- tensor integrator -------
+
+def test_tensor_step_conserves_oscillator_energy():
+    """Hc = 0: implicit midpoint keeps k^2 (h - s/k^2)^2 + h'^2 exactly (quadratic invariant)."""
+    k2, dt, s = 37.0, 0.3, 0.2 + 0.1j
+    h, v = 0.5 - 0.2j, 1.3 + 0.4j
+    e0 = k2 * abs(h - s / k2) ** 2 + abs(v) ** 2
+    for _ in range(1000):
+        h, v = O.tensor_step(h, v, k2, 0.0, dt, s)
+    assert abs(k2 * abs(h - s / k2) ** 2 + abs(v) ** 2 - e0) <= 1e-12 * e0
+
+
+def test_tensor_step_second_order_convergence():
+    k2, s, h0, v0, T = 25.0, 0.3, 0.1, -0.2, 1.0
+    w = math.sqrt(k2)
+    exact = s / k2 + (h0 - s / k2) * math.cos(w * T) + v0 / w * math.sin(w * T)
+    errs = []
+    for nsub in (200, 400, 800):
+        h, v = complex(h0), complex(v0)
+        for _ in range(nsub):
+            h, v = O.tensor_step(h, v, k2, 0.0, T / nsub, s)
+        errs.append(abs(h - exact))
+    assert 3.7 < errs[0] / errs[1] < 4.3 and 3.7 < errs[1] / errs[2] < 4.3
+
+
+def test_tensor_step_hubble_friction_damps():
+    k2, dt = 10.0, 0.05
+    h, v = 1.0 + 0j, 0.0 + 0j
+    e_prev = k2 * abs(h) ** 2 + abs(v) ** 2
+    for _ in range(200):
+        h, v = O.tensor_step(h, v, k2, 0.5, dt, 0.0)
+        e = k2 * abs(h) ** 2 + abs(v) ** 2
+        assert e < e_prev
+        e_prev = e
+
+
+# -------------------------------------------------------- particles ---------
+
+def _fields_mode(n, amp, nv=(1, 2, 0)):
+    f = amp * mode_field(n, nv, 0.2)
+    return f
+
+
+def test_relativistic_update_reduces_to_newtonian_for_slow_particles():
+    """u << a: Eqs. (drift),(kick) -> dx/dtau = u/a, du/dtau = -a grad psi (Sec. 3.2)."""
+    n = 16
+    rng = np.random.default_rng(9)
+    pos = rng.random((50, 3)); a = 0.05
+    mom = rng.standard_normal((50, 3)) * 1e-5 * a
+    phi = _fields_mode(n, 1e-9)  # small enough that the volume factor 3 phi is below the tolerance
+    z = np.zeros((n, n, n)); B = np.zeros((3, n, n, n))
+    p1, u1 = O.kick_drift(n, pos, mom, a, a * 1.01, 0.1, 0.1, phi, z, B)
+    p2, u2 = O.kick_drift(n, pos, mom, a, a * 1.01, 0.1, 0.1, phi, z, B, newtonian=True)
+    assert rel(u1 - mom, u2 - mom) <= 1e-6
+    d1 = (p1 - pos + 0.5) % 1.0 - 0.5; d2 = (p2 - pos + 0.5) % 1.0 - 0.5
+    assert rel(d1, d2) <= 1e-6
+
+
+def test_free_streaming_speed_is_p_over_e():
+    """No metric perturbation: dx/dtau = u / sqrt(a^2 + u^2), below the speed of light."""
+    n = 8
+    rng = np.random.default_rng(10)
+    pos = rng.random((20, 3)) * 0.5 + 0.25; a = 0.01
+    mom = rng.standard_normal((20, 3)) * 0.05
+    z = np.zeros((n, n, n)); B = np.zeros((3, n, n, n))
+    dt = 1e-3
+    p1, u1 = O.kick_drift(n, pos, mom, a, a, dt, dt, z, z, B)
+    v = mom / np.sqrt(a * a + (mom ** 2).sum(1))[:, None]
+    assert rel((p1 - pos) / dt, v) <= 1e-12
+    assert np.all(np.linalg.norm((p1 - pos) / dt, axis=1) < 1.0)
+    assert np.array_equal(u1, mom)
+
+
+def test_light_bending_twice_newtonian():
+    """u >> a, chi = 0: transverse kick -> -2 |u| grad_perp phi (twice the Newtonian deflection)."""
+    n = 16
+    x, y, z = vertex_coords(n)
+    phi = 1e-6 * np.sin(2 * np.pi * y)
+    zero = np.zeros((n, n, n)); B = np.zeros((3, n, n, n))
+    pos = np.array([[0.3, 0.1, 0.5], [0.7, 0.4, 0.2]]); a = 1e-4
+    mom = np.array([[1.0, 0.0, 0.0], [-2.0, 0.0, 0.0]])
+    _, u1 = O.kick_drift(n, pos, mom, a, a, 1.0, 0.0, phi, zero, B)
+    gy = O.cic_interp(O.gradient(phi, 1), pos)
+    ratio = (u1[:, 1] - mom[:, 1]) / (-np.abs(mom[:, 0]) * gy)
+    assert np.allclose(ratio, 2.0, rtol=1e-6)
+
+
+def _unexpanded_rates(a, u, phi, psi, B, dphi, dpsi, dB):
+    """Hamilton's equations of Eq. (1pclH) without expansion, per unit mass, at one particle.
+
+    alpha = a e^psi, gamma^ij = a^-2 e^{2 phi} delta^ij, beta^i = -e^{2 phi} B_i; gradients of the
+    exponentials by the chain rule, dB[i, j] = d_i B_j.
+    """
+    g = math.exp(2 * phi) / a ** 2
+    root = math.sqrt(1.0 + g * (u @ u))
+    alpha = a * math.exp(psi)
+    beta = -math.exp(2 * phi) * B
+    dx = alpha * g * u / root - beta
+    dalpha = alpha * dpsi
+    dbeta = -math.exp(2 * phi) * (dB + 2.0 * np.outer(dphi, B))  # [i, j] = d_i beta^j
+    dg = 2.0 * g * dphi
+    du = -root * dalpha + dbeta @ u - alpha * (u @ u) * dg / (2.0 * root)
+    return dx, du
+
+
+def test_update_matches_unexpanded_hamiltonian_to_second_order():
+    """The expanded kick and drift agree with Eqs. (drift),(kick) up to terms quadratic in the fields."""
+    n = 16
+    rng = np.random.default_rng(11)
+    pos = rng.random((6, 3)) * 0.5 + 0.25; a = 0.1
+    mom = rng.standard_normal((6, 3)) * 0.05
+    err_u, err_x = [], []
+    for amp in (2e-4, 1e-4):
+        phi = amp * mode_field(n, (1, 2, 0), 0.1)
+        chi = 0.3 * amp * mode_field(n, (0, 1, 1), 0.7)
+        B = np.stack([amp * mode_field(n, (2, 0, 1), 0.3 * i) for i in range(3)])
+        _, u1 = O.kick_drift(n, pos, mom, a, a, 1.0, 0.0, phi, chi, B)       # kick only: u1 - u = rate
+        dtd = 1e-3
+        p1, _ = O.kick_drift(n, pos, mom, a, a, 0.0, dtd, phi, chi, B)       # drift only
+        psi = phi - chi
+        eu = ex = 0.0
+        for k in range(len(pos)):
+            pk = pos[k:k + 1]
+            vals = lambda f: O.cic_interp(f, pk)[0]  # noqa: E731
+            grad = lambda f: np.array([O.cic_interp(O.gradient(f, d), pk)[0] for d in range(3)])  # noqa: E731
+            dB = np.array([[O.cic_interp(O.gradient(B[j], i), pk)[0] for j in range(3)] for i in range(3)])
+            Bp = np.array([vals(B[i]) for i in range(3)])
+            dx_ex, du_ex = _unexpanded_rates(a, mom[k], vals(phi), vals(psi), Bp, grad(phi), grad(psi), dB)
+            eu = max(eu, np.max(np.abs((u1[k] - mom[k]) - du_ex)))
+            ex = max(ex, np.max(np.abs((p1[k] - pos[k]) / dtd - dx_ex)))
+        err_u.append(eu); err_x.append(ex)
+    # first-order terms agree; the remainder scales with the square of the amplitude
+    assert 3.5 < err_u[0] / err_u[1] < 4.5
+    assert 3.5 < err_x[0] / err_x[1] < 4.5
+    assert err_u[0] < 1e-2 * 2e-4 and err_x[0] < 10 * (2e-4) ** 2
+
+
+def test_zero_net_momentum_newtonian():
+    """Antisymmetric centred gradient + CIC on both sides: sum of all kicks vanishes (Newtonian mode)."""
+    from paper_2607_17929_gb300 import ics
+    n = 16
+    s = O.OracleSim(n, n ** 3, OM, BOX, 100.0, 0.0, 100, newtonian=True)
+    pos, mom = ics.zeldovich_ics(n, BOX, OM, 0.67, s.a_n[0], s.a_n[0], 7)
+    s.set_particles(pos, mom)
+    s.step()
+    _, u1 = s.particles()
+    du = u1 - mom
+    assert np.linalg.norm(du.sum(0)) <= 1e-12 * np.abs(du).sum()
+
+
+def test_linear_growth_of_plane_wave():
+    """Newtonian mode, one small Zel'dovich plane wave: displacement grows like D(a) of LCDM (z = 100 -> 0)."""
+    from paper_2607_17929_gb300 import ics
+    n = 32
+    s = O.OracleSim(n, n ** 3, OM, BOX, 100.0, 0.0, 100, newtonian=True)
+    a0 = s.a_n[0]
+    a_m = O.a_after(a0, -0.5 * s.dtau[0], OM, s.h0)
+    amp = 1e-4
+    pos, mom = ics.plane_wave_ics(n, amp, 1, a0, a_m, OM, BOX)
+    q = pos.copy()
+    q[:, 0] = (np.arange(n ** 3) % n + 0.5) / n
+    s.set_particles(pos, mom)
+    for _ in range(100):
+        s.step()
+    p1, _ = s.particles()
+    disp = (p1[:, 0] - q[:, 0] + 0.5) % 1.0 - 0.5
+    basis = np.sin(2 * np.pi * q[:, 0])
+    amp_end = -(disp @ basis) / (basis @ basis) * 2 * np.pi
+    d0, _ = ics.growth(a0, OM)
+    d1, _ = ics.growth(1.0, OM)
+    growth_ratio = amp_end / amp
+    # discretisation: CIC window and centred gradient weaken the force on the n=1 mode of a 32 mesh by
+    # about 1.3 %, which lowers the growth over ln(101) e-folds by about 3 %
+    assert abs(growth_ratio / (d1 / d0) - 1.0) <= 0.05
+
+
+def test_power_spectrum_of_random_particles_is_shot_noise():
+    """Poisson particles: CIC-assigned shot noise is prod_i (1 - 2/3 sin^2(pi n_i / N)) / N_p
+    (aliased CIC window of Hockney & Eastwood; Jing 2005)."""
+    n, npart, nb = 32, 32 ** 3, 13
+    pos = np.random.default_rng(12).random((npart, 3))
+    rho = O.deposit_mass(n, pos, OM / npart)
+    k, pk, nm = O.power_spectrum(rho, OM, nb)
+    m = np.fft.fftfreq(n, 1.0 / n)
+    nz, ny, nx = np.meshgrid(m, m, m, indexing="ij")
+    b = np.rint(np.sqrt(nx ** 2 + ny ** 2 + nz ** 2)).astype(int)
+    win = np.prod([1 - (2 / 3) * np.sin(np.pi * c / n) ** 2 for c in (nx, ny, nz)], axis=0)
+    sel = (b >= 1) & (b < nb)
+    expect = win[sel].sum() / npart
+    got = (pk[1:] * nm[1:]).sum()
+    assert nm[1:].sum() == sel.sum()
+    assert abs(got / expect - 1.0) < 0.06

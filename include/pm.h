@@ -1,0 +1,186 @@
+/*
+ * pm.h -- C ABI of libpm, a single-GPU (sm_103a) implementation of one full
+ * relativistic particle-mesh step of gevolution 2.0 (arxiv 2607.17929):
+ * cloud-in-cell projection of the particles' stress-energy, FFT solves of
+ * the scalar (phi, chi), vector (B_i) and tensor (h_ij) metric
+ * perturbations, and the relativistic kick and drift of every particle.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: comoving box length L = 1, c = 1, conformal time tau in units of
+ *   L/c, critical density today = 1, so 4 pi G = 3/2 H0^2 with
+ *   H0 = box_mpch / 2997.92458.  Particle mass m = omega_m / n_part, and
+ *   "momentum" means the canonical momentum per unit mass u_i = q_i / m.
+ * Mesh: vertex-centred N^3 mesh, row-major [z][y][x] with x fastest (the
+ *   "fast" direction of the paper's rod decomposition, Sec. 2, Fig. 1).
+ * Particle arrays passed in or out: [n_part][3] doubles in (x, y, z) order;
+ *   positions in box units, wrapped into [0, 1).  Rows are in particle-id
+ *   order; the id of a particle is its row in the pm_set_particles arrays.
+ * Pointers: any pointer argument may be host memory (pageable or pinned) or
+ *   device memory of the context's device; the library detects which with
+ *   cudaPointerGetAttributes.  Pointers are borrowed for the duration of the
+ *   call only; the library owns all of its device memory.
+ * Streams: all device work is enqueued on cfg->stream (NULL = the legacy
+ *   default stream).  Calls that write host memory synchronise the stream
+ *   before returning; every other call returns once its work is enqueued.
+ * Errors: every call returns a pm_status and never aborts.  The message of
+ *   the last error is kept per context (pm_last_error).  A CUDA error
+ *   reported by the runtime poisons the context: later calls return
+ *   PM_ERR_STATE.  Thread safety: one context must not be used by two host
+ *   threads at once; distinct contexts are independent.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PM_OK = 0,
+    PM_ERR_INVALID_ARG = 1,      /* NULL pointer, bad id, value out of range */
+    PM_ERR_UNSUPPORTED_SIZE = 2, /* n_mesh not of the form 2^a 3^b with a >= 3 in [8, 1024] */
+    PM_ERR_OOM = 3,              /* device allocation failed (nothing leaked) */
+    PM_ERR_CUDA = 4,             /* CUDA runtime error; the context is poisoned */
+    PM_ERR_TIMEOUT = 5,          /* a bounded device wait ran out */
+    PM_ERR_STATE = 6             /* call out of order, poisoned context, schedule exhausted */
+} pm_status;
+
+typedef enum {
+    PM_FP64 = 0,  /* positions cell + f64 offset, f64 momenta, f64 fields and FFTs */
+    PM_MIXED = 1  /* int32 cell + f32 offset, f32 momenta, f32 fields and FFTs;
+                     f64 background, compensated per-cell deposit sums, f64 k=0 mode */
+} pm_precision;
+
+/* flags */
+#define PM_NEWTONIAN 1u /* Newtonian limit (Sec. 3.2): project mass only, Poisson equation
+                           Lap phi = 4 pi G a^-1 (rho - omega_m), chi = B = h = 0,
+                           du/dtau = -a grad phi, dx/dtau = u/a */
+
+typedef struct pm_config {
+    int32_t n_mesh;    /* N: 2^a 3^b, a >= 3, 8 <= N <= 1024 */
+    int32_t n_steps;   /* length of the time-step schedule (>= 1) */
+    int64_t n_part;    /* number of particles, 1 <= n_part < 2^31 */
+    double box_mpch;   /* comoving box side in Mpc/h (> 0) */
+    double omega_m;    /* matter density today, flat LCDM with Omega_L = 1 - omega_m */
+    double z_init;     /* redshift of the first step */
+    double z_final;    /* redshift after the last step (< z_init) */
+    int32_t precision; /* pm_precision */
+    uint32_t flags;    /* PM_NEWTONIAN or 0 */
+    void *stream;      /* cudaStream_t to enqueue on; NULL = default stream */
+} pm_config;
+
+typedef struct pm_ctx pm_ctx;
+
+/* Field ids for pm_get_field.  The potentials are those of the latest solve
+ * (after pm_solve or pm_step: phi_n, chi_n, B_n of step n).  The sources are
+ * those assembled by the latest pm_project (configuration space):
+ *   R     = 4piG a^-2 (S00 - a omega_m) - 3Hc/dtau_{n-1} phi_{n-1} - 3Hc^2 chi_{n-1}
+ *   F_i   = 4piG a^-2 S0i - phi' d_i psi
+ *   Sig_ij = 16piG a^-2 TF(S_ij) - 2 TF[2 d_i phi d_j phi - (d_i phi + d_i psi)(d_j phi + d_j psi)]
+ * (Sig is trace-free; Sig_zz = -Sig_xx - Sig_yy is not stored). */
+enum {
+    PM_FIELD_PHI = 0, PM_FIELD_CHI = 1, PM_FIELD_BX = 2, PM_FIELD_BY = 3, PM_FIELD_BZ = 4,
+    PM_FIELD_R = 5, PM_FIELD_FX = 6, PM_FIELD_FY = 7, PM_FIELD_FZ = 8,
+    PM_FIELD_SXX = 9, PM_FIELD_SXY = 10, PM_FIELD_SXZ = 11, PM_FIELD_SYY = 12, PM_FIELD_SYZ = 13
+};
+
+/* Tensor state ids for pm_get_tensor: helicity amplitudes and their tau derivatives. */
+enum { PM_TENSOR_HPLUS = 0, PM_TENSOR_HCROSS = 1, PM_TENSOR_DHPLUS = 2, PM_TENSOR_DHCROSS = 3 };
+
+/* Stage ids for pm_get_timings (milliseconds of the latest step, CUDA events). */
+enum { PM_T_PROJECT = 0, PM_T_FFT_FWD = 1, PM_T_SOLVE = 2, PM_T_FFT_INV = 3, PM_T_UPDATE = 4,
+       PM_T_SORT = 5, PM_T_STEP = 6, PM_T_COUNT = 7 };
+
+/* Create a context: validates cfg, computes the FP64 background schedule
+ * (Sec. 3.1: Hc = d ln a / d tau, flat LCDM; steps uniform in ln a from
+ * z_init to z_final, tau by 64-point Gauss-Legendre, half-step a by Newton)
+ * and allocates every device buffer on the current device.
+ * On success *out owns the context; free it with pm_destroy.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA. */
+pm_status pm_init(const pm_config *cfg, pm_ctx **out);
+
+/* Release all device and host memory of ctx (NULL is ignored). */
+void pm_destroy(pm_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
+const char *pm_last_error(const pm_ctx *ctx);
+
+/* Load the particle state at step 0: pos, mom [n_part][3] f64 (host or
+ * device).  pos is wrapped into [0,1); the momenta u are those at half a
+ * step before the first step (staggered leap-frog, Sec. 3.1).  Sorts the
+ * particles by cell and runs the quasi-static bootstrap solve that gives
+ * phi_{-1} (phi = chi = 0 in the projection weights, no d/dtau term).
+ * Errors: INVALID_ARG (NULL, NaN/Inf in the input), CUDA, STATE. */
+pm_status pm_set_particles(pm_ctx *ctx, const double *pos, const double *mom);
+
+/* Projection of step n (Eqs. matterstress to first order in phi, psi):
+ * CIC deposit of S00, S0i, TF(S_ij) from the cell-sorted particles with
+ * phi_{n-1}, chi_{n-1} interpolated at the particles, and assembly of the
+ * sources R, F_i, Sig_ij of Eqs. NewtonHc, momentumcontraint, spacespace
+ * with the quadratic terms from the previous step (Sec. 3.1, predictor with
+ * zero iterations).  Errors: STATE (no particles, schedule exhausted), CUDA. */
+pm_status pm_project(pm_ctx *ctx);
+
+/* Field solve of step n: forward r2c FFTs of the sources, Fourier-space
+ * solutions phi_n, chi_n, B_n and one implicit-midpoint step of the tensor
+ * modes (h'' + 2Hc h' + k^2 h = TT source), inverse c2r FFTs.
+ * Errors: STATE (pm_project not called for this step), CUDA. */
+pm_status pm_solve(pm_ctx *ctx);
+
+/* Particle update of step n (Eqs. kick, drift expanded to first order in
+ * phi, psi, B, h neglected): CIC gather of the centred-difference gradients,
+ * kick u_{n+1/2} = u_{n-1/2} + dtau_kick K, drift x_{n+1} = x_n + dtau_n V,
+ * periodic wrap, then a counting sort of the particles by cell.
+ * Advances the step index.  Errors: STATE (pm_solve not called), CUDA. */
+pm_status pm_update(pm_ctx *ctx);
+
+/* pm_project + pm_solve + pm_update. */
+pm_status pm_step(pm_ctx *ctx);
+
+/* Current particle state in id order: pos [n_part][3] (box units, [0,1)),
+ * mom [n_part][3] (u at half a step before the next step).  Either pointer
+ * may be NULL to skip it.  Errors: INVALID_ARG, STATE, CUDA. */
+pm_status pm_get_particles(pm_ctx *ctx, double *pos, double *mom);
+
+/* One N^3 real field as f64 (see PM_FIELD_*), [z][y][x].  Errors: INVALID_ARG, STATE, CUDA. */
+pm_status pm_get_field(pm_ctx *ctx, int field_id, double *dst);
+
+/* One tensor-state array as interleaved complex f64 on the half spectrum
+ * [kz][ky][kx], kx in [0, N/2], N*N*(N/2+1) complex values, in unnormalised
+ * DFT units (sum_x f(x) e^{-i k.x}).  Polarisations: e1 perpendicular to k
+ * from the axis with the smallest |n_i| (ties to the lowest axis),
+ * e2 = khat x e1, e+ = (e1 e1 - e2 e2)/sqrt2, ex = (e1 e2 + e2 e1)/sqrt2. */
+pm_status pm_get_tensor(pm_ctx *ctx, int which, double *dst);
+
+/* Power spectrum of the CIC mass-density contrast delta = rho/omega_m - 1 of
+ * the current particles: P(k_b) = mean |delta_k|^2 / N^6 over modes with
+ * round(|n|) = b, for 1 <= b < nbins; bin 0 is left empty.  Host outputs
+ * k[nbins] (mean |k| = 2 pi |n|), pk[nbins], nmodes[nbins].  Overwrites the
+ * stored sources.  Errors: INVALID_ARG, STATE, CUDA. */
+pm_status pm_power_spectrum(pm_ctx *ctx, int nbins, double *k, double *pk, int64_t *nmodes);
+
+/* Step index (number of completed steps), a at that step, conformal time
+ * since z_init.  Any pointer may be NULL. */
+pm_status pm_get_time(pm_ctx *ctx, int32_t *step, double *a, double *tau);
+
+/* Schedule arrays: a_n[n_steps+1], dtau[n_steps], a_half[n_steps] (host). */
+pm_status pm_get_schedule(pm_ctx *ctx, double *a_n, double *dtau, double *a_half);
+
+/* Stage timings of the latest step in ms (see PM_T_*), n <= PM_T_COUNT. */
+pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n);
+
+/* Checkpoint: write / read the full state (config, step, particles,
+ * phi_{n-1}, chi_{n-1}, phi_{n-2}, tensor state) to / from a host file.
+ * pm_load requires a context created with the same config.
+ * Errors: INVALID_ARG (bad path, config mismatch, corrupt file), STATE, CUDA. */
+pm_status pm_save(pm_ctx *ctx, const char *path);
+pm_status pm_load(pm_ctx *ctx, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PM_H */

@@ -1,0 +1,368 @@
+// Pencil-staged 3D FFT for the metric solves (Sec. 2.3 transforms a 3D
+// field as a sequence of 1D FFTs along x, y and z; here every sequence of
+// 1D transforms runs from shared memory on one GPU).
+//
+// Layout: real fields [z][y][x]; half spectra [kz][ky][kx] with
+// kx in [0, N/2].  Forward: x pass (two real rows packed as one complex
+// line, r2c split), y pass, z pass.  Inverse: z, y, then x (c2r).  No
+// normalisation: the Fourier solve applies 1/N^3.
+//
+// Each pass loads L lines of N points into shared memory as [j][line]
+// (line index fastest, so the strided y and z passes read L contiguous
+// complex values per row: 128-byte segments), runs a Stockham autosort
+// FFT (Govindaraju et al., SC'08 formulation) with radices 8, 4, 2 and 3
+// in registers, and writes the lines back.
+#include "pm_internal.cuh"
+
+namespace pm {
+
+FftPlan make_plan(int n)
+{
+    FftPlan p{};
+    p.n = n;
+    int m = n;
+    while (m % 3 == 0) { p.radix[p.nst++] = 3; m /= 3; }
+    while (m % 8 == 0) { p.radix[p.nst++] = 8; m /= 8; }
+    if (m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
+    if (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
+    return p;
+}
+
+namespace {
+
+template <class C> __device__ __forceinline__ C mk(decltype(C::x) x, decltype(C::x) y)
+{
+    C r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <class C> __device__ __forceinline__ C add(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C sub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <class C> __device__ __forceinline__ C mul(C a, C b)
+{
+    return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// z * (s i), s = +-1
+template <class C> __device__ __forceinline__ C mul_si(C z, int s)
+{
+    return s > 0 ? mk<C>(-z.y, z.x) : mk<C>(z.y, -z.x);
+}
+template <class C> __device__ __forceinline__ C scale(C z, decltype(C::x) f) { return mk<C>(z.x * f, z.y * f); }
+
+// In-register DFTs of size R with exponent sign s (-1 forward, +1 inverse).
+template <int R, class C> struct Dft;
+
+template <class C> struct Dft<2, C> {
+    static __device__ __forceinline__ void run(C *v, int)
+    {
+        C a = v[0], b = v[1];
+        v[0] = add(a, b);
+        v[1] = sub(a, b);
+    }
+};
+
+template <class C> struct Dft<4, C> {
+    static __device__ __forceinline__ void run(C *v, int s)
+    {
+        C t0 = add(v[0], v[2]), t1 = sub(v[0], v[2]);
+        C t2 = add(v[1], v[3]), t3 = mul_si(sub(v[1], v[3]), s);
+        v[0] = add(t0, t2);
+        v[2] = sub(t0, t2);
+        v[1] = add(t1, t3);
+        v[3] = sub(t1, t3);
+    }
+};
+
+template <class C> struct Dft<8, C> {
+    static __device__ __forceinline__ void run(C *v, int s)
+    {
+        using T = decltype(C::x);
+        const T h = (T)0.70710678118654752440084436210484903928;
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, C>::run(e, s);
+        Dft<4, C>::run(o, s);
+        // o_k * W8^k,  W8 = exp(s i pi / 4)
+        C o1 = scale(add(o[1], mul_si(o[1], s)), h);
+        C o2 = mul_si(o[2], s);
+        C o3 = scale(sub(mul_si(o[3], s), o[3]), h);
+        v[0] = add(e[0], o[0]);
+        v[4] = sub(e[0], o[0]);
+        v[1] = add(e[1], o1);
+        v[5] = sub(e[1], o1);
+        v[2] = add(e[2], o2);
+        v[6] = sub(e[2], o2);
+        v[3] = add(e[3], o3);
+        v[7] = sub(e[3], o3);
+    }
+};
+
+template <class C> struct Dft<3, C> {
+    static __device__ __forceinline__ void run(C *v, int s)
+    {
+        using T = decltype(C::x);
+        const T r3 = (T)0.86602540378443864676372317075293618347;
+        C t = add(v[1], v[2]);
+        C d = mul_si(scale(sub(v[1], v[2]), r3), s);
+        C m = sub(v[0], scale(t, (T)0.5));
+        v[0] = add(v[0], t);
+        v[1] = add(m, d);
+        v[2] = sub(m, d);
+    }
+};
+
+// One Stockham stage over L lines held in shared memory as buf[j * L + line].
+template <int R, int MAXB, class C>
+__device__ __forceinline__ void stage(C *buf, int n, int L, int Ns, const C *tw, int s)
+{
+    const int nbl = n / R;
+    const int total = nbl * L;
+    C v[MAXB][R];
+#pragma unroll
+    for (int q = 0; q < MAXB; q++) {
+        int g = threadIdx.x + q * blockDim.x;
+        if (g < total) {
+            int l = g % L, b = g / L;
+#pragma unroll
+            for (int r = 0; r < R; r++) v[q][r] = buf[(b + r * nbl) * L + l];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MAXB; q++) {
+        int g = threadIdx.x + q * blockDim.x;
+        if (g < total) {
+            int l = g % L, b = g / L;
+            int k = b % Ns;
+            int step = k * (n / (Ns * R));
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                C w = tw[r * step];
+                if (s > 0) w.y = -w.y;
+                v[q][r] = mul(v[q][r], w);
+            }
+            Dft<R, C>::run(v[q], s);
+            int j0 = (b - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; r++) buf[(j0 + r * Ns) * L + l] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Full N-point transform of L lines.  Requires L * n <= 16 * blockDim.x.
+template <class C>
+__device__ void fft_lines(C *buf, int L, const FftPlan &plan, const C *tw, int s)
+{
+    int Ns = 1;
+    for (int st = 0; st < plan.nst; st++) {
+        int R = plan.radix[st];
+        if (R == 8) stage<8, 2>(buf, plan.n, L, Ns, tw, s);
+        else if (R == 4) stage<4, 4>(buf, plan.n, L, Ns, tw, s);
+        else if (R == 2) stage<2, 8>(buf, plan.n, L, Ns, tw, s);
+        else stage<3, 6>(buf, plan.n, L, Ns, tw, s);
+        Ns *= R;
+    }
+}
+
+template <class T> constexpr int fft_block() { return sizeof(T) == 8 ? 256 : 512; }
+
+// Strided column pass (y or z): line g = (batch b, column c), point j at
+// data[b * stride_b + j * stride_j + c].
+template <class T>
+__global__ void __launch_bounds__(fft_block<T>())
+k_fft_cols(Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t stride_j,
+           int64_t ncols, int64_t stride_b, int64_t nlines, int s)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = plan.n;
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf = tw + n;
+    int64_t *lbase = reinterpret_cast<int64_t *>(buf + (size_t)L * n);
+    C *data = reinterpret_cast<C *>(ptrs.p[blockIdx.y]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const int64_t g0 = (int64_t)blockIdx.x * L;
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        int64_t g = g0 + l;
+        lbase[l] = g < nlines ? (g / ncols) * stride_b + (g % ncols) : -1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
+        int l = e % L, j = e / L;
+        int64_t base = lbase[l];
+        C v = mk<C>(0, 0);
+        if (base >= 0) v = data[base + j * stride_j];
+        buf[e] = v;
+    }
+    __syncthreads();
+    fft_lines(buf, L, plan, tw, s);
+    for (int e = threadIdx.x; e < L * n; e += blockDim.x) {
+        int l = e % L, j = e / L;
+        int64_t base = lbase[l];
+        if (base >= 0) data[base + j * stride_j] = buf[e];
+    }
+}
+
+// x pass, forward: real rows 2l, 2l+1 packed as z = a + i b, one complex
+// FFT, then A_k = (Z_k + conj Z_{N-k})/2, B_k = -i (Z_k - conj Z_{N-k})/2.
+template <class T>
+__global__ void __launch_bounds__(fft_block<T>())
+k_fft_r2c(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t npairs)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = plan.n, h = n / 2 + 1;
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf = tw + n;
+    T *bufr = reinterpret_cast<T *>(buf);
+    const T *src = reinterpret_cast<const T *>(in.p[blockIdx.y]);
+    C *dst = reinterpret_cast<C *>(out.p[blockIdx.y]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const int64_t p0 = (int64_t)blockIdx.x * L;
+    for (int e = threadIdx.x; e < 2 * L * n; e += blockDim.x) {
+        int l2 = e / n, x = e % n;
+        int l = l2 >> 1, comp = l2 & 1;
+        int64_t pair = p0 + l;
+        T v = 0;
+        if (pair < npairs) v = src[(2 * pair + comp) * n + x];
+        bufr[2 * (x * L + l) + comp] = v;
+    }
+    __syncthreads();
+    fft_lines(buf, L, plan, tw, -1);
+    for (int e = threadIdx.x; e < L * h; e += blockDim.x) {
+        int l = e / h, k = e % h;
+        int64_t pair = p0 + l;
+        if (pair >= npairs) continue;
+        C zk = buf[k * L + l], zn = buf[((n - k) % n) * L + l];
+        const T half = (T)0.5;
+        C A = mk<C>(half * (zk.x + zn.x), half * (zk.y - zn.y));
+        C B = mk<C>(half * (zk.y + zn.y), -half * (zk.x - zn.x));
+        dst[(2 * pair) * h + k] = A;
+        dst[(2 * pair + 1) * h + k] = B;
+    }
+}
+
+// x pass, inverse: half spectra A (row 2l), B (row 2l+1) -> Z = A + i B over
+// the full line by Hermitian extension (imaginary parts at k = 0 and N/2
+// dropped), inverse FFT, a = Re z, b = Im z.
+template <class T>
+__global__ void __launch_bounds__(fft_block<T>())
+k_fft_c2r(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t npairs)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = plan.n, h = n / 2 + 1;
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf = tw + n;
+    const T *bufr = reinterpret_cast<const T *>(buf);
+    const C *src = reinterpret_cast<const C *>(in.p[blockIdx.y]);
+    T *dst = reinterpret_cast<T *>(out.p[blockIdx.y]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
+    const int64_t p0 = (int64_t)blockIdx.x * L;
+    for (int e = threadIdx.x; e < L * h; e += blockDim.x) {
+        int l = e / h, k = e % h;
+        int64_t pair = p0 + l;
+        C A = mk<C>(0, 0), B = mk<C>(0, 0);
+        if (pair < npairs) {
+            A = src[(2 * pair) * h + k];
+            B = src[(2 * pair + 1) * h + k];
+        }
+        if (k == 0 || 2 * k == n) {
+            A.y = 0;
+            B.y = 0;
+        }
+        buf[k * L + l] = mk<C>(A.x - B.y, A.y + B.x);
+        if (k > 0 && 2 * k < n) buf[(n - k) * L + l] = mk<C>(A.x + B.y, B.x - A.y);
+    }
+    __syncthreads();
+    fft_lines(buf, L, plan, tw, +1);
+    for (int e = threadIdx.x; e < 2 * L * n; e += blockDim.x) {
+        int l2 = e / n, x = e % n;
+        int l = l2 >> 1, comp = l2 & 1;
+        int64_t pair = p0 + l;
+        if (pair < npairs) dst[(2 * pair + comp) * n + x] = bufr[2 * (x * L + l) + comp];
+    }
+}
+
+template <class T> int lines_per_block(int n) { return (16 * fft_block<T>()) / n; }
+
+template <class T> size_t cols_smem(int n, int L)
+{
+    return sizeof(typename Cplx<T>::type) * ((size_t)L * n + n) + sizeof(int64_t) * L;
+}
+
+template <class T> void set_smem_attrs()
+{
+    static bool done = false;
+    if (done) return;
+    done = true;
+    const int maxs = 160 * 1024;
+    cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    cudaFuncSetAttribute(k_fft_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    cudaFuncSetAttribute(k_fft_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+}
+
+template <class T>
+void col_pass(Ctx &c, int nf, const Ptrs &p, int64_t stride_j, int64_t ncols, int64_t stride_b, int64_t nlines,
+              int s)
+{
+    int L = lines_per_block<T>(c.N);
+    dim3 grid((unsigned)((nlines + L - 1) / L), nf);
+    k_fft_cols<T><<<grid, fft_block<T>(), cols_smem<T>(c.N, L), c.stream>>>(
+        p, reinterpret_cast<const typename Cplx<T>::type *>(c.tw), c.plan, L, stride_j, ncols, stride_b, nlines,
+        s);
+}
+
+}  // namespace
+
+template <class T>
+void fft_forward(Ctx &c, int nf, const void *const *real_in, void *const *spec_out)
+{
+    set_smem_attrs<T>();
+    const int N = c.N;
+    const int64_t h = N / 2 + 1;
+    Ptrs pi{}, po{};
+    for (int i = 0; i < nf; i++) {
+        pi.p[i] = const_cast<void *>(real_in[i]);
+        po.p[i] = spec_out[i];
+    }
+    // x: real rows -> half-spectrum rows.  L complex lines = L row pairs per block.
+    int L = lines_per_block<T>(N);
+    int64_t npairs = (int64_t)N * N / 2;
+    dim3 grid((unsigned)((npairs + L - 1) / L), nf);
+    k_fft_r2c<T><<<grid, fft_block<T>(), cols_smem<T>(N, L), c.stream>>>(
+        pi, po, reinterpret_cast<const typename Cplx<T>::type *>(c.tw), c.plan, L, npairs);
+    // y: lines (z, kx), points stride h
+    col_pass<T>(c, nf, po, h, h, (int64_t)N * h, (int64_t)N * h, -1);
+    // z: lines (ky, kx), points stride N h
+    col_pass<T>(c, nf, po, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, -1);
+}
+
+template <class T>
+void fft_inverse(Ctx &c, int nf, void *const *spec_in, void *const *real_out)
+{
+    set_smem_attrs<T>();
+    const int N = c.N;
+    const int64_t h = N / 2 + 1;
+    Ptrs pi{}, po{};
+    for (int i = 0; i < nf; i++) {
+        pi.p[i] = spec_in[i];
+        po.p[i] = real_out[i];
+    }
+    col_pass<T>(c, nf, pi, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, +1);
+    col_pass<T>(c, nf, pi, h, h, (int64_t)N * h, (int64_t)N * h, +1);
+    int L = lines_per_block<T>(N);
+    int64_t npairs = (int64_t)N * N / 2;
+    dim3 grid((unsigned)((npairs + L - 1) / L), nf);
+    k_fft_c2r<T><<<grid, fft_block<T>(), cols_smem<T>(N, L), c.stream>>>(
+        pi, po, reinterpret_cast<const typename Cplx<T>::type *>(c.tw), c.plan, L, npairs);
+}
+
+template void fft_forward<double>(Ctx &, int, const void *const *, void *const *);
+template void fft_forward<float>(Ctx &, int, const void *const *, void *const *);
+template void fft_inverse<double>(Ctx &, int, void *const *, void *const *);
+template void fft_inverse<float>(Ctx &, int, void *const *, void *const *);
+
+}  // namespace pm

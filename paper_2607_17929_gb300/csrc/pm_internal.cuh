@@ -1,0 +1,156 @@
+// Internal declarations of libpm (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pm.h"
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Precision traits.  FP64: f64 everywhere.  Mixed: f32 offsets, momenta,
+// fields and FFTs; per-cell deposit sums in compensated f32 (float-float,
+// about 48 significant bits) and the k = 0 mode in f64.
+// ---------------------------------------------------------------------------
+template <class T> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+
+// Particle record: cell index + offset inside the cell + momentum + id.
+// 32 bytes in mixed precision, 64 bytes in FP64 (one/two 32-byte sectors).
+template <class T> struct alignas(16) Particle;
+template <> struct alignas(16) Particle<float> {
+    int32_t cell;
+    uint32_t id;
+    float f[3];
+    float u[3];
+};
+template <> struct alignas(16) Particle<double> {
+    int32_t cell;
+    uint32_t id;
+    double f[3];
+    double u[3];
+    double pad;
+};
+static_assert(sizeof(Particle<float>) == 32, "mixed particle must be 32 B");
+static_assert(sizeof(Particle<double>) == 64, "fp64 particle must be 64 B");
+
+// Up to 16 device pointers for batched multi-field launches.
+struct Ptrs {
+    void *p[16];
+};
+
+// Per-step scalars (computed in FP64 on the host).
+struct StepScalars {
+    double a;            // a_n
+    double hc;           // Hc(a_n)
+    double c_phi_dt;     // 3 Hc / dtau_{n-1} (0 in the bootstrap and Newtonian mode)
+    double c_phi_h2;     // 3 Hc^2 (0 in Newtonian mode)
+    double inv_dtau_prev2;  // 1 / dtau_{n-2} for phi'
+    double dtau;         // dtau_n (tensor step, drift)
+    double dtau_kick;    // (dtau_{n-1} + dtau_n) / 2
+    double a_half;       // a_{n+1/2}
+    double hc_half;      // Hc(a_{n+1/2})
+    double four_pi_g;
+    double mass;
+    double omega_m;
+    int newtonian;
+    int bootstrap;
+};
+
+struct FftPlan {
+    int n;
+    int nst;
+    int radix[12];
+};
+
+FftPlan make_plan(int n);
+
+// ---------------------------------------------------------------------------
+// Context.
+// ---------------------------------------------------------------------------
+struct Ctx {
+    pm_config cfg;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool poisoned = false;
+    std::string err;
+    int N = 0;
+    int64_t nc = 0;    // N^3
+    int64_t nh = 0;    // N * N * (N/2 + 1)
+    int64_t np = 0;
+    bool mixed = false;
+    bool newtonian = false;
+
+    // schedule (host, FP64)
+    std::vector<double> a_n, dtau, a_half;
+    double h0 = 0, four_pi_g = 0, mass = 0;
+    int step = 0;           // completed steps
+    int stage = 0;          // 0: ready to project, 1: projected, 2: solved
+    bool have_particles = false;
+
+    // device buffers
+    void *part[2] = {nullptr, nullptr};  // Particle<T> ping-pong
+    int cur = 0;
+    int32_t *count = nullptr;   // nc
+    int32_t *start = nullptr;   // nc + 1
+    int32_t *blocksum = nullptr;
+    int64_t nblocksum = 0;
+    void *phi[3] = {nullptr, nullptr, nullptr};  // ring: phi_{n-2}, phi_{n-1}, phi_n
+    int iphi_prev2 = 0, iphi_prev = 1, iphi_new = 2;
+    void *chi = nullptr;        // chi_{n-1} before the solve, chi_n after it
+    void *B = nullptr;          // 3 * nc
+    void *src = nullptr;        // 9 * nc real sources
+    void *spec = nullptr;       // 9 * nh complex
+    void *tens = nullptr;       // 4 * nh complex tensor state
+    void *ktab = nullptr;       // N values of ktilde(n)
+    void *tw = nullptr;         // N twiddles exp(-2 pi i k / N)
+    double *dscal = nullptr;    // device f64 scalars: [0] k=0 particle sum, [1] mean phi_{n-1}, [2] mean phi_n
+    void *stage_buf = nullptr;  // host-transfer staging (f64)
+    int64_t stage_elems = 0;
+    FftPlan plan;
+
+    cudaEvent_t ev[8] = {};
+    double t_ms[PM_T_COUNT] = {};
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (implemented in pm_fft.cu, pm_particles.cu, pm_solve.cu).
+// ---------------------------------------------------------------------------
+template <class T>
+void fft_forward(Ctx &c, int nfields, const void *const *real_in, void *const *spec_out);
+template <class T>
+void fft_inverse(Ctx &c, int nfields, void *const *spec_in, void *const *real_out);
+
+template <class T>
+void launch_project(Ctx &c, const StepScalars &s);
+template <class T>
+void launch_solve(Ctx &c, const StepScalars &s);
+template <class T>
+void launch_kick_drift(Ctx &c, const StepScalars &s);
+template <class T>
+void launch_sort(Ctx &c);
+template <class T>
+void launch_load_particles(Ctx &c, const double *d_pos, const double *d_mom, int64_t first, int64_t count);
+template <class T>
+void launch_store_particles(Ctx &c, double *d_pos, double *d_mom, int64_t first, int64_t count);
+template <class T>
+void launch_store_particles_scatter(Ctx &c, double *d_pos, double *d_mom);
+template <class T>
+void launch_density(Ctx &c, void *real_out);
+template <class T>
+void launch_pk_bin(Ctx &c, const void *spec_in, int nbins, double *d_acc);
+template <class T>
+void launch_to_f64(Ctx &c, const void *src, double *dst, int64_t n);
+template <class T>
+void launch_from_f64(Ctx &c, const double *src, void *dst, int64_t n);
+template <class T>
+void launch_check_finite(Ctx &c, const double *d, int64_t n, int *d_flag);
+
+void launch_scan(Ctx &c);
+
+}  // namespace pm

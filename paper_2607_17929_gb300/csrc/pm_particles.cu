@@ -1,0 +1,807 @@
+// Particle-mesh kernels: stress-energy projection, gather + kick + drift,
+// counting sort by cell, particle I/O.
+//
+// Projection (Sec. 2.1 "particle-mesh projection", Eqs. matterstress):
+// particles are kept sorted by cell.  One CTA owns an 8^3 tile of mesh
+// vertices and pulls every particle whose CIC cloud touches the tile (the
+// 9^3 cells [x0-1, x0+8)), computes its charges once into shared memory and
+// lets each thread accumulate the 9 source components of its own vertex in
+// registers.  No global atomics, and every mesh value is written once with
+// coalesced stores.  The same kernel assembles the configuration-space
+// sources of the field equations from phi_{n-1}, chi_{n-1}, phi_{n-2}.
+#include "pm_internal.cuh"
+
+namespace pm {
+
+namespace {
+
+constexpr int TILE = 8;
+constexpr int REG = TILE + 1;        // 9 source cells per axis
+constexpr int FLD = TILE + 2;        // 10 field vertices per axis
+constexpr int NREG = REG * REG * REG;  // 729
+constexpr int NFLD = FLD * FLD * FLD;  // 1000
+constexpr int DEP_THREADS = TILE * TILE * TILE;  // 512
+constexpr int NK0SLOTS = 1024;
+
+// Per-cell accumulator.  FP64: plain double.  Mixed: float-float with
+// Knuth's TwoSum, so a cell sum keeps about 48 significant bits.
+template <class T> struct Acc;
+template <> struct Acc<double> {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double hi() const { return s; }
+    __device__ __forceinline__ double lo() const { return 0.0; }
+};
+template <> struct Acc<float> {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float x)
+    {
+        float t = __fadd_rn(s, x);
+        float bp = __fsub_rn(t, s);
+        float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+    __device__ __forceinline__ float hi() const { return s; }
+    __device__ __forceinline__ float lo() const { return c; }
+};
+
+template <class T> __device__ __forceinline__ T mulr(T a, T b);
+template <> __device__ __forceinline__ float mulr<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mulr<double>(double a, double b) { return __dmul_rn(a, b); }
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <class T> struct DepParams {
+    const Particle<T> *part;
+    const int32_t *start;
+    const T *phi1;   // phi_{n-1}
+    const T *chi1;   // chi_{n-1}
+    const T *phi2;   // phi_{n-2}
+    Ptrs out;        // R, Fx, Fy, Fz, Sxx, Sxy, Sxz, Syy, Syz
+    double *k0slots; // NK0SLOTS partial sums of the k = 0 excess
+    int N, nt;
+    int full;        // 1: relativistic sources; 0: R only (bootstrap / Newtonian)
+    int use_fields;  // phi/chi enter the charges (not in the bootstrap / Newtonian mode)
+    int newtonian;
+    T a, a2, mass;
+    T G;             // 4piG a^-2 N^3 (Newtonian: 4piG a^-1 N^3)
+    T rb_hi, rb_lo;  // expected per-vertex charge sum of a uniform load, float-float split
+    T c1, c2;        // 3Hc/dtau_{n-1}, 3Hc^2
+    T inv_dt2;       // 1/dtau_{n-2}
+    T halfN;         // N/2 (centred difference 1/(2 dx))
+};
+
+template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 1536; }
+
+static_assert((sizeof(double) * (2 * NFLD + 12 * 640)) % 8 == 0 && (sizeof(float) * (2 * NFLD + 12 * 1536)) % 8 == 0,
+              "shared-memory T arrays must end on an 8-byte boundary");
+
+template <class T> size_t dep_smem()
+{
+    return sizeof(T) * (2 * NFLD + 12 * dep_cap<T>()) + sizeof(int) * (3 * NREG + 64) + sizeof(double) * 32;
+}
+
+// Exclusive scan of v[0..n) (n <= 2 * blockDim) in place; returns the total.
+__device__ int block_exclusive_scan(int *v, int n, int *warp_tmp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int a = (2 * tid < n) ? v[2 * tid] : 0;
+    int b = (2 * tid + 1 < n) ? v[2 * tid + 1] : 0;
+    int s = a + b, x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int w = lane < nw ? warp_tmp[lane] : 0, z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < nw) warp_tmp[lane] = z - w;
+        if (lane == nw - 1) warp_tmp[32] = z;
+    }
+    __syncthreads();
+    int excl = warp_tmp[wid] + x - s;
+    if (2 * tid < n) v[2 * tid] = excl;
+    if (2 * tid + 1 < n) v[2 * tid + 1] = excl + a;
+    int total = warp_tmp[32];
+    __syncthreads();
+    return total;
+}
+
+template <class T>
+__global__ void __launch_bounds__(DEP_THREADS) k_project(DepParams<T> p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int CAP = dep_cap<T>();
+    T *sphi = reinterpret_cast<T *>(smem);
+    T *schi = sphi + NFLD;
+    T *sq = schi + NFLD;          // [9][CAP] charges
+    T *sf = sq + 9 * CAP;         // [3][CAP] offsets
+    // the T arrays span a multiple of 8 bytes, so the f64 scratch stays aligned
+    double *sred = reinterpret_cast<double *>(sf + 3 * CAP);  // 32 doubles
+    int *scnt = reinterpret_cast<int *>(sred + 32);
+    int *soff = scnt + NREG;
+    int *sgs = soff + NREG;
+    int *wtmp = sgs + NREG;       // 64 ints
+
+    const int N = p.N, nt = p.nt, tid = threadIdx.x;
+    const int b = blockIdx.x;
+    const int x0 = (b % nt) * TILE, y0 = ((b / nt) % nt) * TILE, z0 = (b / (nt * nt)) * TILE;
+
+    // potentials of the previous solve on the 10^3 vertices [x0-1, x0+8]
+    for (int i = tid; i < NFLD; i += DEP_THREADS) {
+        int rx = i % FLD, ry = (i / FLD) % FLD, rz = i / (FLD * FLD);
+        int64_t g = ((int64_t)wrapi(z0 - 1 + rz, N) * N + wrapi(y0 - 1 + ry, N)) * N + wrapi(x0 - 1 + rx, N);
+        sphi[i] = p.use_fields ? p.phi1[g] : T(0);
+        schi[i] = p.use_fields ? p.chi1[g] : T(0);
+    }
+    // particle ranges of the 9^3 source cells [x0-1, x0+8)
+    for (int i = tid; i < NREG; i += DEP_THREADS) {
+        int sx = i % REG, sy = (i / REG) % REG, sz = i / (REG * REG);
+        int64_t g = ((int64_t)wrapi(z0 - 1 + sz, N) * N + wrapi(y0 - 1 + sy, N)) * N + wrapi(x0 - 1 + sx, N);
+        int gs = p.start[g];
+        scnt[i] = p.start[g + 1] - gs;
+        soff[i] = scnt[i];
+        sgs[i] = gs;
+    }
+    __syncthreads();
+    const int total = block_exclusive_scan(soff, NREG, wtmp);
+
+    const int ox = tid % TILE, oy = (tid / TILE) % TILE, oz = tid / (TILE * TILE);
+    Acc<T> acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; c++) acc[c].zero();
+    double k0 = 0.0;
+    const int ncomp = p.full ? 9 : 1;
+
+    for (int lo = 0; lo < total; lo += CAP) {
+        const int hi = min(total, lo + CAP);
+        for (int i = lo + tid; i < hi; i += DEP_THREADS) {
+            // source cell of local particle i: largest t with soff[t] <= i
+            int t0 = 0, t1 = NREG - 1;
+            while (t0 < t1) {
+                int m = (t0 + t1 + 1) >> 1;
+                if (soff[m] <= i) t0 = m;
+                else t1 = m - 1;
+            }
+            const int t = t0;
+            const Particle<T> P = p.part[sgs[t] + (i - soff[t])];
+            const int sx = t % REG, sy = (t / REG) % REG, sz = t / (REG * REG);
+            const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
+            const int j = i - lo;
+            sf[j] = fx;
+            sf[CAP + j] = fy;
+            sf[2 * CAP + j] = fz;
+            if (!p.full && p.newtonian) {
+                sq[j] = p.mass;
+                continue;
+            }
+            T ph = 0, ch = 0;
+            if (p.use_fields) {
+                const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+#pragma unroll
+                for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+                    for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                        for (int dx = 0; dx < 2; dx++) {
+                            const T w = wx[dx] * wy[dy] * wz[dz];
+                            const int v = (sx + dx) + FLD * ((sy + dy) + FLD * (sz + dz));
+                            ph += w * sphi[v];
+                            ch += w * schi[v];
+                        }
+            }
+            const T ux = P.u[0], uy = P.u[1], uz = P.u[2];
+            const T u2 = ux * ux + uy * uy + uz * uz;
+            const T E = sqrt(p.a2 + u2);
+            const T iE = T(1) / E;
+            const T v2 = u2 * iE * iE;
+            const T m = p.mass;
+            // T^00 charge and its excess over a particle at rest (k = 0 mode in FP64)
+            sq[j] = m * E * (T(1) + T(3) * ph + ph * v2);
+            if (sx >= 1 && sy >= 1 && sz >= 1) {
+                const T excess = m * (u2 / (E + p.a) + E * (T(3) * ph + ph * v2));
+                k0 += (double)excess;
+            }
+            if (p.full) {
+                const T wv = m * (T(1) + T(4) * ph - ch);
+                sq[CAP + j] = wv * ux;
+                sq[2 * CAP + j] = wv * uy;
+                sq[3 * CAP + j] = wv * uz;
+                const T ws = m * (T(1) + T(3) * ph - ph * v2) * iE;
+                const T txx = ws * ux * ux, tyy = ws * uy * uy, tzz = ws * uz * uz;
+                const T tr3 = (txx + tyy + tzz) * T(1.0 / 3.0);
+                sq[4 * CAP + j] = txx - tr3;
+                sq[5 * CAP + j] = ws * ux * uy;
+                sq[6 * CAP + j] = ws * ux * uz;
+                sq[7 * CAP + j] = tyy - tr3;
+                sq[8 * CAP + j] = ws * uy * uz;
+            }
+        }
+        __syncthreads();
+        // vertex (ox, oy, oz) receives from source cells (o - d), d in {0,1}^3,
+        // with weight (d ? f : 1 - f) per axis
+#pragma unroll
+        for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+            for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 2; dx++) {
+                    const int ts = (ox + 1 - dx) + REG * ((oy + 1 - dy) + REG * (oz + 1 - dz));
+                    const int jb = max(soff[ts], lo), je = min(soff[ts] + scnt[ts], hi);
+                    for (int jj = jb; jj < je; jj++) {
+                        const int j = jj - lo;
+                        const T gx = sf[j], gy = sf[CAP + j], gz = sf[2 * CAP + j];
+                        const T w = (dx ? gx : T(1) - gx) * (dy ? gy : T(1) - gy) * (dz ? gz : T(1) - gz);
+#pragma unroll
+                        for (int c = 0; c < 9; c++)
+                            if (c < ncomp) acc[c].add(mulr(w, sq[c * CAP + j]));
+                    }
+                }
+        __syncthreads();
+    }
+
+    // k = 0 excess: block reduction in FP64, one atomic per CTA into a slot
+    {
+        double v = k0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) sred[tid >> 5] = v;
+        __syncthreads();
+        if (tid < 32) {
+            v = tid < (DEP_THREADS >> 5) ? sred[tid] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (tid == 0 && !p.newtonian) atomicAdd(&p.k0slots[b & (NK0SLOTS - 1)], v);
+        }
+    }
+
+    // epilogue: assemble the field-equation sources at vertex o
+    const int64_t go = ((int64_t)(z0 + oz) * N + (y0 + oy)) * N + (x0 + ox);
+    const int vo = (ox + 1) + FLD * ((oy + 1) + FLD * (oz + 1));
+    const T phc = sphi[vo], chc = schi[vo];
+    // R: the uniform background a*Omega_m is removed before rounding
+    const T dS = (acc[0].hi() - p.rb_hi) + (acc[0].lo() - p.rb_lo);
+    reinterpret_cast<T *>(p.out.p[0])[go] = p.G * dS - p.c1 * phc - p.c2 * chc;
+    if (!p.full) return;
+    T gphi[3], gpsi[3];
+    const int st[3] = {1, FLD, FLD * FLD};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const T dp = (sphi[vo + st[d]] - sphi[vo - st[d]]) * p.halfN;
+        const T dc = (schi[vo + st[d]] - schi[vo - st[d]]) * p.halfN;
+        gphi[d] = dp;
+        gpsi[d] = dp - dc;
+    }
+    const T dphi = (phc - p.phi2[go]) * p.inv_dt2;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        reinterpret_cast<T *>(p.out.p[1 + d])[go] = p.G * (acc[1 + d].hi() + acc[1 + d].lo()) - dphi * gpsi[d];
+    T Q[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) Q[i][j] = T(2) * gphi[i] * gphi[j] - (gphi[i] + gpsi[i]) * (gphi[j] + gpsi[j]);
+    const T trQ3 = (Q[0][0] + Q[1][1] + Q[2][2]) * T(1.0 / 3.0);
+    const T G4 = T(4) * p.G;
+    const T Sxx = G4 * (acc[4].hi() + acc[4].lo()) - T(2) * (Q[0][0] - trQ3);
+    const T Sxy = G4 * (acc[5].hi() + acc[5].lo()) - T(2) * Q[0][1];
+    const T Sxz = G4 * (acc[6].hi() + acc[6].lo()) - T(2) * Q[0][2];
+    const T Syy = G4 * (acc[7].hi() + acc[7].lo()) - T(2) * (Q[1][1] - trQ3);
+    const T Syz = G4 * (acc[8].hi() + acc[8].lo()) - T(2) * Q[1][2];
+    reinterpret_cast<T *>(p.out.p[4])[go] = Sxx;
+    reinterpret_cast<T *>(p.out.p[5])[go] = Sxy;
+    reinterpret_cast<T *>(p.out.p[6])[go] = Sxz;
+    reinterpret_cast<T *>(p.out.p[7])[go] = Syy;
+    reinterpret_cast<T *>(p.out.p[8])[go] = Syz;
+}
+
+// Sum the k = 0 slots: dscal[0] = sum over particles of the T^00 excess.
+__global__ void k_k0_reduce(double *dscal)
+{
+    __shared__ double s[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < NK0SLOTS; i += blockDim.x) v += dscal[8 + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) dscal[0] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather + kick + drift (Eqs. kick, drift to first order, Sec. 3.1):
+//   du_i/dtau = -E d_i psi - (u^2/E) d_i phi - u_j d_i B_j,  E = sqrt(a_n^2 + u^2)
+//   dx^i/dtau = (u_i/E')(1 + 3 phi - chi - phi u'^2/E'^2) + B_i,  E' at a_{n+1/2}
+// with mesh gradients (f(x+dx) - f(x-dx)) / (2 dx) interpolated by CIC, i.e. a
+// 4x2x2 stencil per direction.  Newtonian mode: du = -a grad phi, dx = u/a.
+// The new cell of each particle is counted for the sort.
+// ---------------------------------------------------------------------------
+template <class T> struct KdParams {
+    Particle<T> *part;
+    int32_t *count;
+    const T *phi, *chi, *Bx, *By, *Bz;
+    int64_t np;
+    int N;
+    int newtonian;
+    T a, a2, a_half2, inv_a_half, dt_kick, dt_drift_N, halfN;
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) k_kick_drift(KdParams<T> p)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.np) return;
+    Particle<T> P = p.part[i];
+    const int N = p.N;
+    const int ix = P.cell % N, iy = (P.cell / N) % N, iz = P.cell / (N * N);
+    const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
+    int xs[4], ys[4], zs[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        xs[k] = wrapi(ix - 1 + k, N);
+        ys[k] = wrapi(iy - 1 + k, N);
+        zs[k] = wrapi(iz - 1 + k, N);
+    }
+    // value weights W(0) = 1-f, W(1) = f; gradient weights over offsets -1..2
+    const T hn = p.halfN;
+    const T Wx[4] = {0, T(1) - fx, fx, 0}, Wy[4] = {0, T(1) - fy, fy, 0}, Wz[4] = {0, T(1) - fz, fz, 0};
+    const T Gx[4] = {-(T(1) - fx) * hn, -fx * hn, (T(1) - fx) * hn, fx * hn};
+    const T Gy[4] = {-(T(1) - fy) * hn, -fy * hn, (T(1) - fy) * hn, fy * hn};
+    const T Gz[4] = {-(T(1) - fz) * hn, -fz * hn, (T(1) - fz) * hn, fz * hn};
+    const int nf = p.newtonian ? 1 : 5;
+    const T *F[5] = {p.phi, p.chi, p.Bx, p.By, p.Bz};
+    T val[5] = {0, 0, 0, 0, 0};
+    T grd[5][3] = {};
+#pragma unroll
+    for (int kz = 0; kz < 4; kz++)
+#pragma unroll
+        for (int ky = 0; ky < 4; ky++)
+#pragma unroll
+            for (int kx = 0; kx < 4; kx++) {
+                const bool cx = (kx == 1 || kx == 2), cy = (ky == 1 || ky == 2), cz = (kz == 1 || kz == 2);
+                if ((int)!cx + (int)!cy + (int)!cz > 1) continue;
+                const T wv = Wx[kx] * Wy[ky] * Wz[kz];
+                const T wgx = (cy && cz) ? Gx[kx] * Wy[ky] * Wz[kz] : T(0);
+                const T wgy = (cx && cz) ? Wx[kx] * Gy[ky] * Wz[kz] : T(0);
+                const T wgz = (cx && cy) ? Wx[kx] * Wy[ky] * Gz[kz] : T(0);
+                const int64_t g = ((int64_t)zs[kz] * N + ys[ky]) * N + xs[kx];
+#pragma unroll
+                for (int q = 0; q < 5; q++) {
+                    if (q >= nf) break;
+                    const T v = __ldg(F[q] + g);
+                    val[q] += wv * v;
+                    grd[q][0] += wgx * v;
+                    grd[q][1] += wgy * v;
+                    grd[q][2] += wgz * v;
+                }
+            }
+    T u[3] = {P.u[0], P.u[1], P.u[2]};
+    T dx[3];
+    if (p.newtonian) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) u[d] -= p.dt_kick * p.a * grd[0][d];
+#pragma unroll
+        for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * u[d] * p.inv_a_half;
+    } else {
+        const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const T E = sqrt(p.a2 + u2);
+        const T u2E = u2 / E;
+        T K[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const T dpsi = grd[0][d] - grd[1][d];
+            K[d] = -E * dpsi - u2E * grd[0][d] - (u[0] * grd[2][d] + u[1] * grd[3][d] + u[2] * grd[4][d]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) u[d] += p.dt_kick * K[d];
+        const T v2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const T Ed = sqrt(p.a_half2 + v2);
+        const T iEd = T(1) / Ed;
+        const T fac = (T(1) + T(3) * val[0] - val[1] - val[0] * v2 * iEd * iEd) * iEd;
+#pragma unroll
+        for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * (u[d] * fac + val[2 + d]);
+    }
+    // new offsets and cell (periodic), cell units
+    const T fo[3] = {fx, fy, fz};
+    const int io[3] = {ix, iy, iz};
+    int inew[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        T f = fo[d] + dx[d];
+        T fl = floor(f);
+        f -= fl;
+        // a finite move is far below N cells; anything else (NaN, Inf) keeps the cell
+        int carry = (fabs(fl) < (T)N) ? (int)fl : 0;
+        if (f >= T(1)) {
+            f = T(0);
+            carry += 1;
+        }
+        int c = (io[d] + carry) % N;
+        if (c < 0) c += N;
+        inew[d] = c;
+        P.f[d] = f;
+        P.u[d] = u[d];
+    }
+    P.cell = (inew[2] * N + inew[1]) * N + inew[0];
+    p.part[i] = P;
+    atomicAdd(&p.count[P.cell], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Counting sort by cell: exclusive scan of the per-cell counts, then scatter.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 1024, SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+__device__ int block_scan_1024(int x, int *wt, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) wt[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = wt[lane], z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        wt[lane] = z - w;
+        if (lane == 31) wt[32] = z;
+    }
+    __syncthreads();
+    int r = wt[wid] + v - x;
+    *total = wt[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const int32_t *cnt, int64_t n, int32_t *bsum)
+{
+    __shared__ int wt[33];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + (int64_t)k * SCAN_T + threadIdx.x;
+        if (i < n) s += cnt[i];
+    }
+    int tot;
+    block_scan_1024(s, wt, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_top(int32_t *bsum, int64_t nb, int32_t *start_end)
+{
+    __shared__ int wt[33];
+    int carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_T) {
+        int64_t i = b0 + threadIdx.x;
+        int x = i < nb ? bsum[i] : 0;
+        int tot;
+        int e = block_scan_1024(x, wt, &tot);
+        if (i < nb) bsum[i] = carry + e;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *start_end = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(const int32_t *cnt, int64_t n, const int32_t *bsum,
+                                                       int32_t *start)
+{
+    __shared__ int wt[33];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + k;
+        v[k] = i < n ? cnt[i] : 0;
+        s += v[k];
+    }
+    int tot;
+    int e = block_scan_1024(s, wt, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + k;
+        if (i < n) start[i] = e;
+        e += v[k];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_scatter(const Particle<T> *in, Particle<T> *out, int64_t np,
+                                                 const int32_t *start, int32_t *count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const Particle<T> P = in[i];
+    const int r = atomicSub(&count[P.cell], 1) - 1;
+    out[start[P.cell] + r] = P;
+}
+
+// ---------------------------------------------------------------------------
+// Particle I/O: f64 (x, y, z) rows <-> cell + offset records.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_load(const double *pos, const double *mom, int64_t first, int64_t cnt, int N,
+                       Particle<T> *out, int32_t *count)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    Particle<T> P{};
+    int ic[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double x = pos[3 * k + d];
+        x -= floor(x);
+        if (x >= 1.0) x = 0.0;
+        double s = x * N;
+        double fl = floor(s);
+        int c = (int)fl;
+        double f = s - fl;
+        if (c >= N) c -= N;
+        ic[d] = c;
+        P.f[d] = (T)f;
+        if (P.f[d] >= T(1)) {  // rounding of f to the storage type
+            P.f[d] = T(0);
+            ic[d] = (c + 1) % N;
+        }
+        P.u[d] = (T)mom[3 * k + d];
+    }
+    P.cell = (ic[2] * N + ic[1]) * N + ic[0];
+    P.id = (uint32_t)(first + k);
+    out[first + k] = P;
+    atomicAdd(&count[P.cell], 1);
+}
+
+template <class T>
+__global__ void k_unpermute(const Particle<T> *in, Particle<T> *out, int64_t np)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const Particle<T> P = in[i];
+    out[P.id] = P;
+}
+
+template <class T>
+__global__ void k_store(const Particle<T> *byid, int64_t first, int64_t cnt, int N, double *pos, double *mom)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    const Particle<T> P = byid[first + k];
+    const int ic[3] = {P.cell % N, (P.cell / N) % N, P.cell / (N * N)};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (pos) pos[3 * k + d] = ((double)ic[d] + (double)P.f[d]) / (double)N;
+        if (mom) mom[3 * k + d] = (double)P.u[d];
+    }
+}
+
+// CIC mass density contrast delta = rho/omega_m - 1 (diagnostic, global FP64 atomics).
+template <class T>
+__global__ void k_density_acc(const Particle<T> *part, int64_t np, int N, double q, double *rho)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const Particle<T> P = part[i];
+    const int ix = P.cell % N, iy = (P.cell / N) % N, iz = P.cell / (N * N);
+    const double f[3] = {(double)P.f[0], (double)P.f[1], (double)P.f[2]};
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++) {
+                const double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+                const int64_t g = ((int64_t)wrapi(iz + dz, N) * N + wrapi(iy + dy, N)) * N + wrapi(ix + dx, N);
+                atomicAdd(&rho[g], q * w);
+            }
+}
+
+template <class T>
+__global__ void k_density_fin(const double *rho, int64_t n, T *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (T)(rho[i] - 1.0);
+}
+
+template <class T> __global__ void k_to_f64(const T *s, double *d, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = (double)s[i];
+}
+
+template <class T> __global__ void k_from_f64(const double *s, T *d, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = (T)s[i];
+}
+
+__global__ void k_check_finite(const double *d, int64_t n, int *flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(d[i])) *flag = 1;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+template <class T>
+void launch_project(Ctx &c, const StepScalars &s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dep_smem<T>());
+        attr = true;
+    }
+    DepParams<T> p{};
+    p.part = reinterpret_cast<const Particle<T> *>(c.part[c.cur]);
+    p.start = c.start;
+    p.phi1 = reinterpret_cast<const T *>(c.phi[c.iphi_prev]);
+    p.chi1 = reinterpret_cast<const T *>(c.chi);
+    p.phi2 = reinterpret_cast<const T *>(c.phi[c.iphi_prev2]);
+    for (int i = 0; i < 9; i++) p.out.p[i] = reinterpret_cast<T *>(c.src) + (size_t)i * c.nc;
+    p.k0slots = c.dscal + 8;
+    p.N = c.N;
+    p.nt = c.N / TILE;
+    p.newtonian = s.newtonian;
+    p.full = !(s.newtonian || s.bootstrap);
+    p.use_fields = p.full;
+    p.a = (T)s.a;
+    p.a2 = (T)(s.a * s.a);
+    p.mass = (T)s.mass;
+    const double n3 = (double)c.nc;
+    double rb;
+    if (s.newtonian) {
+        p.G = (T)(s.four_pi_g / s.a * n3);
+        rb = s.omega_m / n3;
+    } else {
+        p.G = (T)(s.four_pi_g / (s.a * s.a) * n3);
+        rb = s.a * s.omega_m / n3;
+    }
+    p.rb_hi = (T)rb;
+    p.rb_lo = (T)(rb - (double)p.rb_hi);
+    p.c1 = (T)s.c_phi_dt;
+    p.c2 = (T)s.c_phi_h2;
+    p.inv_dt2 = (T)s.inv_dtau_prev2;
+    p.halfN = (T)(0.5 * c.N);
+    cudaMemsetAsync(c.dscal + 8, 0, sizeof(double) * NK0SLOTS, c.stream);
+    const int ntiles = (c.N / TILE) * (c.N / TILE) * (c.N / TILE);
+    k_project<T><<<ntiles, DEP_THREADS, dep_smem<T>(), c.stream>>>(p);
+    k_k0_reduce<<<1, 1024, 0, c.stream>>>(c.dscal);
+}
+
+template <class T>
+void launch_kick_drift(Ctx &c, const StepScalars &s)
+{
+    KdParams<T> p{};
+    p.part = reinterpret_cast<Particle<T> *>(c.part[c.cur]);
+    p.count = c.count;
+    const T *B = reinterpret_cast<const T *>(c.B);
+    p.phi = reinterpret_cast<const T *>(c.phi[c.iphi_new]);
+    p.chi = reinterpret_cast<const T *>(c.chi);
+    p.Bx = B;
+    p.By = B + c.nc;
+    p.Bz = B + 2 * c.nc;
+    p.np = c.np;
+    p.N = c.N;
+    p.newtonian = s.newtonian;
+    p.a = (T)s.a;
+    p.a2 = (T)(s.a * s.a);
+    p.a_half2 = (T)(s.a_half * s.a_half);
+    p.inv_a_half = (T)(1.0 / s.a_half);
+    p.dt_kick = (T)s.dtau_kick;
+    p.dt_drift_N = (T)(s.dtau * c.N);
+    p.halfN = (T)(0.5 * c.N);
+    k_kick_drift<T><<<nblk(c.np, 256), 256, 0, c.stream>>>(p);
+}
+
+void launch_scan(Ctx &c)
+{
+    const int64_t nb = (c.nc + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, c.stream>>>(c.count, c.nc, c.blocksum);
+    k_scan_top<<<1, SCAN_T, 0, c.stream>>>(c.blocksum, nb, c.start + c.nc);
+    k_scan_down<<<(unsigned)nb, SCAN_T, 0, c.stream>>>(c.count, c.nc, c.blocksum, c.start);
+}
+
+template <class T>
+void launch_sort(Ctx &c)
+{
+    launch_scan(c);
+    const int o = 1 - c.cur;
+    k_scatter<T><<<nblk(c.np, 256), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[c.cur]),
+                                                         reinterpret_cast<Particle<T> *>(c.part[o]), c.np,
+                                                         c.start, c.count);
+    c.cur = o;
+}
+
+template <class T>
+void launch_load_particles(Ctx &c, const double *d_pos, const double *d_mom, int64_t first, int64_t count)
+{
+    k_load<T><<<nblk(count, 256), 256, 0, c.stream>>>(d_pos, d_mom, first, count, c.N,
+                                                      reinterpret_cast<Particle<T> *>(c.part[c.cur]), c.count);
+}
+
+template <class T>
+void launch_store_particles_scatter(Ctx &c, double *, double *)
+{
+    const int o = 1 - c.cur;
+    k_unpermute<T><<<nblk(c.np, 256), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[c.cur]),
+                                                           reinterpret_cast<Particle<T> *>(c.part[o]), c.np);
+}
+
+template <class T>
+void launch_store_particles(Ctx &c, double *d_pos, double *d_mom, int64_t first, int64_t count)
+{
+    const int o = 1 - c.cur;
+    k_store<T><<<nblk(count, 256), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[o]), first,
+                                                       count, c.N, d_pos, d_mom);
+}
+
+template <class T>
+void launch_density(Ctx &c, void *real_out)
+{
+    double *rho = reinterpret_cast<double *>(c.spec);  // scratch: nc doubles fit in the spectra block
+    cudaMemsetAsync(rho, 0, sizeof(double) * c.nc, c.stream);
+    const double q = (double)c.nc / (double)c.np;  // N^3 m / omega_m
+    k_density_acc<T><<<nblk(c.np, 256), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[c.cur]),
+                                                             c.np, c.N, q, rho);
+    k_density_fin<T><<<nblk(c.nc, 256), 256, 0, c.stream>>>(rho, c.nc, reinterpret_cast<T *>(real_out));
+}
+
+template <class T>
+void launch_to_f64(Ctx &c, const void *src, double *dst, int64_t n)
+{
+    k_to_f64<T><<<nblk(n, 256), 256, 0, c.stream>>>(reinterpret_cast<const T *>(src), dst, n);
+}
+
+template <class T>
+void launch_from_f64(Ctx &c, const double *src, void *dst, int64_t n)
+{
+    k_from_f64<T><<<nblk(n, 256), 256, 0, c.stream>>>(src, reinterpret_cast<T *>(dst), n);
+}
+
+template <class T>
+void launch_check_finite(Ctx &c, const double *d, int64_t n, int *d_flag)
+{
+    k_check_finite<<<nblk(n, 256), 256, 0, c.stream>>>(d, n, d_flag);
+}
+
+#define PM_INST(T)                                                                          \
+    template void launch_project<T>(Ctx &, const StepScalars &);                            \
+    template void launch_kick_drift<T>(Ctx &, const StepScalars &);                         \
+    template void launch_sort<T>(Ctx &);                                                    \
+    template void launch_load_particles<T>(Ctx &, const double *, const double *, int64_t,  \
+                                           int64_t);                                        \
+    template void launch_store_particles<T>(Ctx &, double *, double *, int64_t, int64_t);   \
+    template void launch_store_particles_scatter<T>(Ctx &, double *, double *);             \
+    template void launch_density<T>(Ctx &, void *);                                         \
+    template void launch_to_f64<T>(Ctx &, const void *, double *, int64_t);                 \
+    template void launch_from_f64<T>(Ctx &, const double *, void *, int64_t);               \
+    template void launch_check_finite<T>(Ctx &, const double *, int64_t, int *);
+PM_INST(double)
+PM_INST(float)
+
+}  // namespace pm

@@ -1,0 +1,260 @@
+"""Python binding of libpm's C ABI (include/pm.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays may
+be torch tensors (CUDA or CPU) or numpy arrays; the library itself decides
+whether a pointer is host or device memory.  There is no fallback: if
+libpm.so is missing the import fails with instructions.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libpm.so")
+
+PM_OK, PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED_SIZE, PM_ERR_OOM, PM_ERR_CUDA, PM_ERR_TIMEOUT, PM_ERR_STATE = range(7)
+STATUS_NAMES = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_UNSUPPORTED_SIZE", 3: "PM_ERR_OOM",
+                4: "PM_ERR_CUDA", 5: "PM_ERR_TIMEOUT", 6: "PM_ERR_STATE"}
+PM_FP64, PM_MIXED = 0, 1
+PM_NEWTONIAN = 1
+FIELDS = {"phi": 0, "chi": 1, "Bx": 2, "By": 3, "Bz": 4, "R": 5, "Fx": 6, "Fy": 7, "Fz": 8,
+          "Sxx": 9, "Sxy": 10, "Sxz": 11, "Syy": 12, "Syz": 13}
+TENSORS = {"h+": 0, "hx": 1, "h+'": 2, "hx'": 3}
+TIMINGS = ["project", "fft_fwd", "solve", "fft_inv", "kick_drift", "sort", "step"]
+
+
+class pm_config(C.Structure):
+    _fields_ = [("n_mesh", C.c_int32), ("n_steps", C.c_int32), ("n_part", C.c_int64),
+                ("box_mpch", C.c_double), ("omega_m", C.c_double), ("z_init", C.c_double),
+                ("z_final", C.c_double), ("precision", C.c_int32), ("flags", C.c_uint32),
+                ("stream", C.c_void_p)]
+
+
+class PMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(_SO):
+        raise ImportError(f"{_SO} is missing: build it with `python -m paper_2607_17929_gb300.build` "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    L = C.CDLL(_SO)
+    vp, dp, i32, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int64
+    sig = {
+        "pm_init": ([C.POINTER(pm_config), C.POINTER(vp)], C.c_int),
+        "pm_destroy": ([vp], None),
+        "pm_last_error": ([vp], C.c_char_p),
+        "pm_set_particles": ([vp, vp, vp], C.c_int),
+        "pm_project": ([vp], C.c_int),
+        "pm_solve": ([vp], C.c_int),
+        "pm_update": ([vp], C.c_int),
+        "pm_step": ([vp], C.c_int),
+        "pm_get_particles": ([vp, vp, vp], C.c_int),
+        "pm_get_field": ([vp, C.c_int, vp], C.c_int),
+        "pm_get_tensor": ([vp, C.c_int, vp], C.c_int),
+        "pm_power_spectrum": ([vp, C.c_int, dp, dp, C.POINTER(i64)], C.c_int),
+        "pm_get_time": ([vp, C.POINTER(i32), dp, dp], C.c_int),
+        "pm_get_schedule": ([vp, dp, dp, dp], C.c_int),
+        "pm_get_timings": ([vp, dp, C.c_int], C.c_int),
+        "pm_save": ([vp, C.c_char_p], C.c_int),
+        "pm_load": ([vp, C.c_char_p], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_project", "pm_solve",
+            "pm_update", "pm_step", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
+            "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
+
+
+def _ptr(a):
+    """Raw data pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(ctx, st):
+    if st != PM_OK:
+        msg = lib.pm_last_error(ctx).decode() if ctx else ""
+        raise PMError(st, msg)
+
+
+def pm_init(n_mesh, n_part, box_mpch, omega_m, z_init, z_final=0.0, n_steps=100, precision=PM_FP64, flags=0,
+            stream=None):
+    """Create a context; returns an opaque handle (int).  stream: a torch.cuda.Stream, raw handle or None."""
+    cfg = pm_config(int(n_mesh), int(n_steps), int(n_part), float(box_mpch), float(omega_m), float(z_init),
+                    float(z_final), int(precision), int(flags), None)
+    if stream is not None:
+        cfg.stream = getattr(stream, "cuda_stream", stream)
+    h = C.c_void_p()
+    st = lib.pm_init(C.byref(cfg), C.byref(h))
+    if st != PM_OK:
+        raise PMError(st, "pm_init rejected the configuration or could not allocate")
+    return h.value
+
+
+def pm_destroy(ctx):
+    lib.pm_destroy(ctx)
+
+
+def pm_last_error(ctx):
+    return lib.pm_last_error(ctx).decode()
+
+
+def pm_set_particles(ctx, pos, mom):
+    _check(ctx, lib.pm_set_particles(ctx, _ptr(pos), _ptr(mom)))
+
+
+def pm_project(ctx):
+    _check(ctx, lib.pm_project(ctx))
+
+
+def pm_solve(ctx):
+    _check(ctx, lib.pm_solve(ctx))
+
+
+def pm_update(ctx):
+    _check(ctx, lib.pm_update(ctx))
+
+
+def pm_step(ctx):
+    _check(ctx, lib.pm_step(ctx))
+
+
+def pm_get_particles(ctx, pos, mom):
+    _check(ctx, lib.pm_get_particles(ctx, _ptr(pos), _ptr(mom)))
+
+
+def pm_get_field(ctx, field, dst):
+    fid = FIELDS[field] if isinstance(field, str) else int(field)
+    _check(ctx, lib.pm_get_field(ctx, fid, _ptr(dst)))
+
+
+def pm_get_tensor(ctx, which, dst):
+    wid = TENSORS[which] if isinstance(which, str) else int(which)
+    _check(ctx, lib.pm_get_tensor(ctx, wid, _ptr(dst)))
+
+
+def pm_power_spectrum(ctx, nbins):
+    k = np.zeros(nbins); pk = np.zeros(nbins); nm = np.zeros(nbins, dtype=np.int64)
+    _check(ctx, lib.pm_power_spectrum(ctx, nbins, k.ctypes.data_as(C.POINTER(C.c_double)),
+                                      pk.ctypes.data_as(C.POINTER(C.c_double)),
+                                      nm.ctypes.data_as(C.POINTER(C.c_int64))))
+    return k, pk, nm
+
+
+def pm_get_time(ctx):
+    s = C.c_int32(); a = C.c_double(); t = C.c_double()
+    _check(ctx, lib.pm_get_time(ctx, C.byref(s), C.byref(a), C.byref(t)))
+    return s.value, a.value, t.value
+
+
+def pm_get_schedule(ctx, n_steps):
+    a = np.zeros(n_steps + 1); dt = np.zeros(n_steps); ah = np.zeros(n_steps)
+    dp = C.POINTER(C.c_double)
+    _check(ctx, lib.pm_get_schedule(ctx, a.ctypes.data_as(dp), dt.ctypes.data_as(dp), ah.ctypes.data_as(dp)))
+    return a, dt, ah
+
+
+def pm_get_timings(ctx):
+    ms = np.zeros(len(TIMINGS))
+    _check(ctx, lib.pm_get_timings(ctx, ms.ctypes.data_as(C.POINTER(C.c_double)), len(TIMINGS)))
+    return dict(zip(TIMINGS, ms.tolist()))
+
+
+def pm_save(ctx, path):
+    _check(ctx, lib.pm_save(ctx, os.fsencode(path)))
+
+
+def pm_load(ctx, path):
+    _check(ctx, lib.pm_load(ctx, os.fsencode(path)))
+
+
+class PM:
+    """Convenience owner of one context; all methods call the functions above."""
+
+    def __init__(self, n_mesh, n_part, box_mpch, omega_m, z_init, z_final=0.0, n_steps=100, precision=PM_FP64,
+                 flags=0, stream=None):
+        self.n = int(n_mesh)
+        self.np = int(n_part)
+        self.n_steps = int(n_steps)
+        self.ctx = pm_init(n_mesh, n_part, box_mpch, omega_m, z_init, z_final, n_steps, precision, flags, stream)
+
+    def close(self):
+        if self.ctx:
+            pm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_particles(self, pos, mom):
+        pm_set_particles(self.ctx, pos, mom)
+
+    def step(self):
+        pm_step(self.ctx)
+
+    def project(self):
+        pm_project(self.ctx)
+
+    def solve(self):
+        pm_solve(self.ctx)
+
+    def update(self):
+        pm_update(self.ctx)
+
+    def particles(self):
+        pos = np.zeros((self.np, 3)); mom = np.zeros((self.np, 3))
+        pm_get_particles(self.ctx, pos, mom)
+        return pos, mom
+
+    def field(self, name):
+        out = np.zeros((self.n, self.n, self.n))
+        pm_get_field(self.ctx, name, out)
+        return out
+
+    def tensor(self, name):
+        out = np.zeros(2 * self.n * self.n * (self.n // 2 + 1))
+        pm_get_tensor(self.ctx, name, out)
+        return out.view(np.complex128).reshape(self.n, self.n, self.n // 2 + 1)
+
+    def power_spectrum(self, nbins):
+        return pm_power_spectrum(self.ctx, nbins)
+
+    def time(self):
+        return pm_get_time(self.ctx)
+
+    def schedule(self):
+        return pm_get_schedule(self.ctx, self.n_steps)
+
+    def timings(self):
+        return pm_get_timings(self.ctx)
+
+    def save(self, path):
+        pm_save(self.ctx, path)
+
+    def load(self, path):
+        pm_load(self.ctx, path)

@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark of one full relativistic particle-mesh step on GB300.
+
+Workload: 512^3 mesh and 512^3 particles, periodic box 2000 Mpc/h, flat LCDM
+(Omega_m = 0.31, h = 0.67), Zel'dovich initial conditions at z = 100 from a
+seeded BBKS Gaussian random field (sigma_8 = 0.8), 100-step schedule in ln a;
+mixed precision (int32 cell + f32 offsets, f32 fields and FFTs, f64
+background, compensated cell sums, f64 k = 0 mode).  One step = projection of
+all stress-energy components, forward FFTs, scalar/vector/tensor solves,
+inverse FFTs, gather + kick + drift, counting sort.
+
+Metric: particle-updates/s = particles / step time (whole job over all ranks),
+timed with CUDA events on the library's stream over K steps after W warm-up
+steps.  The FP64 path is timed on the same workload for the mixed-vs-FP64
+speed-up.  ``--impl reference`` times the FP64 CPU oracle instead.
+
+Multi-GPU: independent replicas (the step does not shard without exchange
+steps), one box per rank, weak scaling; no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+OM, H, ZI, SEED = 0.31, 0.67, 100.0, 3
+N_STEPS_SCHEDULE = 100
+CELL_MPCH = 2000.0 / 512  # comoving cell size of the workload
+
+# kernels whose compulsory DRAM bytes are modelled (per launch)
+KERNELS = ["project", "fft_fwd_x", "fft_fwd_y", "fft_fwd_z", "solve", "fft_inv_z", "fft_inv_y", "fft_inv_x",
+           "kick_drift", "scan", "scatter"]
+KERNEL_SOURCE = {"project": "pm_particles.cu", "kick_drift": "pm_particles.cu", "scan": "pm_particles.cu",
+                 "scatter": "pm_particles.cu", "solve": "pm_solve.cu"}
+
+
+def kernel_bytes(name, n, n_part, mixed):
+    """Compulsory DRAM bytes of one launch: every input read once, every output written once."""
+    ts = 4 if mixed else 8
+    cs = 2 * ts
+    ps = 32 if mixed else 64
+    nc = n ** 3
+    nh = n * n * (n // 2 + 1)
+    return {
+        "project": ps * n_part + 4 * (nc + 1) + 3 * ts * nc + 9 * ts * nc,
+        "fft_fwd_x": 9 * ts * nc + 9 * cs * nh,
+        "fft_fwd_y": 2 * 9 * cs * nh,
+        "fft_fwd_z": 2 * 9 * cs * nh,
+        "solve": 9 * cs * nh + 5 * cs * nh + 2 * 4 * cs * nh,
+        "fft_inv_z": 2 * 5 * cs * nh,
+        "fft_inv_y": 2 * 5 * cs * nh,
+        "fft_inv_x": 5 * cs * nh + 5 * ts * nc,
+        "kick_drift": 2 * ps * n_part + 5 * ts * nc + 8 * nc,
+        "scan": 4 * nc + 4 * (nc + 1),
+        "scatter": 2 * ps * n_part + 4 * nc + 8 * nc,
+    }[name]
+
+
+def survey_bytes_per_update(mixed):
+    """Minimum bytes per particle update of the method (140 B/particle + 288 B/cell mixed; twice for FP64)."""
+    return 428.0 if mixed else 816.0
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_sha(fname):
+    p = os.path.join(ROOT, "paper_2607_17929_gb300", "csrc", fname)
+    try:
+        return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+
+
+def ncu_traffic(kernel, n, n_part, mixed):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this launch, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) < 6 or line.startswith("#"):
+            continue
+        kname, prec, ncap, bytes_cap, src, sha = parts[:6]
+        if kname != kernel or prec != ("mixed" if mixed else "fp64"):
+            continue
+        if source_sha(src) != sha:
+            return None
+        scale = (n ** 3) / float(int(ncap) ** 3)
+        return float(bytes_cap) * scale
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = str(device_index)
+        try:  # address the physical GPU by PCI bus id when torch exposes it
+            import torch
+            pr = torch.cuda.get_device_properties(device_index)
+            self.dev = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            if vis and vis.split(",")[0].strip().isdigit():
+                self.dev = vis.split(",")[0].strip()
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def make_ics(n, box, seed, a0, a_m):
+    from paper_2607_17929_gb300 import ics
+    return ics.zeldovich_ics(n, box, OM, H, a0, a_m, seed)
+
+
+def half_step_back(a0, dtau0, box):
+    """a at tau_0 - dtau_0/2 from the library's own schedule scalars (Newton on the conformal-time integral)."""
+    h0 = box / 2997.92458
+    def hc(a):
+        return a * h0 * math.sqrt(OM / a ** 3 + 1 - OM)
+    # Gauss-Legendre 16 points is ample for half a step
+    import numpy as np
+    x, w = np.polynomial.legendre.leggauss(16)
+    def tau(a_lo, a_hi):
+        m, r = 0.5 * (a_lo + a_hi), 0.5 * (a_hi - a_lo)
+        return r * sum(wi / ((m + r * xi) * hc(m + r * xi)) for xi, wi in zip(x, w))
+    a = a0 * math.exp(-0.5 * dtau0 * hc(a0))
+    for _ in range(50):
+        g = tau(a, a0) - 0.5 * dtau0
+        a += g * a * hc(a)
+    return a
+
+
+def cpu_oracle_rate(n, steps, box):
+    """Particle updates per second of the FP64 C oracle (single thread) on an n^3 sample."""
+    from oracle import oracle as O
+    s = O.OracleSim(n, n ** 3, OM, box, ZI, 0.0, N_STEPS_SCHEDULE)
+    a_m = O.a_after(s.a_n[0], -0.5 * s.dtau[0], OM, s.h0)
+    pos, mom = make_ics(n, box, SEED, s.a_n[0], a_m)
+    s.set_particles(pos, mom)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = 64
+    box = CELL_MPCH * n
+    from oracle import oracle as O
+    s = O.OracleSim(n, n ** 3, OM, box, ZI, 0.0, N_STEPS_SCHEDULE)
+    a_m = O.a_after(s.a_n[0], -0.5 * s.dtau[0], OM, s.h0)
+    pos, mom = make_ics(n, box, SEED, s.a_n[0], a_m)
+    s.set_particles(pos, mom)
+    for _ in range(args.warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt
+    sample = f"{args.steps} oracle steps of the same recipe at {n}^3 (box {box:.0f} Mpc/h, same cell size)"
+    line = {
+        "impl": "reference", "metric": "particle-updates/s per full PM step", "value": value,
+        "unit": "particle-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "relativistic PM step (FP64 CPU oracle) on a bounded sample of the 512^3 workload",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pm", choices=["pm", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="mesh side (particles = n^3)")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2607_17929_gb300 import build
+    build.build()
+    from paper_2607_17929_gb300 import pm
+
+    n = args.n
+    n_part = n ** 3
+    box = CELL_MPCH * n
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # inputs: the same seeded initial conditions for every rank's replica (seed offset per rank)
+    probe = pm.PM(8, 8, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED)
+    a_n, dtau, _ = probe.schedule()
+    probe.close()
+    a_m = half_step_back(a_n[0], dtau[0], box)
+    t_ic = time.perf_counter()
+    pos, mom = make_ics(n, box, SEED + rank, a_n[0], a_m)
+    t_ic = time.perf_counter() - t_ic
+    d_pos = torch.from_numpy(pos).cuda()
+    d_mom = torch.from_numpy(mom).cuda()
+
+    def timed_run(precision, warmup, steps):
+        sim = pm.PM(n, n_part, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, precision, 0, stream)
+        sim.set_particles(d_pos, d_mom)
+        for _ in range(warmup):
+            sim.step()
+        torch.cuda.synchronize()
+        pm.pm_get_timings(sim.ctx)  # open a fresh timing window
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps):
+                sim.step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        ms = ev0.elapsed_time(ev1) / steps
+        per_kernel, launches = pm.pm_get_timings(sim.ctx)
+        return sim, ms, per_kernel, launches, clk.summary()
+
+    sim, ms_mixed, kern, launches, clocks = timed_run(pm.PM_MIXED, args.warmup, args.steps)
+    ms_max = max_over_ranks(ms_mixed)
+    value = world * n_part / (ms_max * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers: upload the state, step, read it back
+    h_pos = torch.from_numpy(pos).pin_memory()
+    h_mom = torch.from_numpy(mom).pin_memory()
+    o_pos = torch.empty_like(h_pos).pin_memory()
+    o_mom = torch.empty_like(h_mom).pin_memory()
+    sim.put_particles(h_pos, h_mom)
+    sim.step()
+    pm.pm_get_particles(sim.ctx, o_pos, o_mom)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sim.put_particles(h_pos, h_mom)
+        sim.step()
+        pm.pm_get_particles(sim.ctx, o_pos, o_mom)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.e2e_steps)
+    sim.close()
+    del sim
+
+    # FP64 path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        sim64, ms64, kern64, _, _ = timed_run(pm.PM_FP64, 2, args.fp64_steps)
+        sim64.close()
+        ms64 = max_over_ranks(ms64)
+        fp64 = {"ms_per_step": ms64, "value": world * n_part / (ms64 * 1e-3),
+                "speedup_mixed_over_fp64": ms64 / ms_max,
+                "kernels_ms": {k: round(v, 4) for k, v in kern64.items()},
+                "step_roofline_frac": survey_bytes_per_update(False) * n_part / (ms64 * 1e-3) / 1e9 /
+                load_peaks()[0]}
+        del sim64
+    torch.cuda.empty_cache()
+
+    # roofline of the dominant kernel
+    peak, peak_kind = load_peaks()
+    dom = max(KERNELS, key=lambda k: kern.get(k, 0.0))
+    alg = kernel_bytes(dom, n, n_part, True)
+    achieved = alg / (kern[dom] * 1e-3) / 1e9
+    src = KERNEL_SOURCE.get(dom, "pm_fft.cu")
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": ncu_traffic(dom, n, n_part, True), "algorithmic_bytes": alg,
+                "launch_ms": round(kern[dom], 4)}
+    per_kernel_frac = {k: round(kernel_bytes(k, n, n_part, True) / (kern[k] * 1e-3) / 1e9 / peak, 3)
+                       for k in KERNELS if kern.get(k, 0) > 0}
+    design_bytes = sum(kernel_bytes(k, n, n_part, True) for k in KERNELS)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        nc_ = 96
+        rate, dt = cpu_oracle_rate(nc_, 2, CELL_MPCH * nc_)
+        cpu = {"value": rate, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"2 steps of the same recipe at {nc_}^3 (box {CELL_MPCH * nc_:.0f} Mpc/h, same cell "
+                         f"size) after its bootstrap, single thread, {dt:.1f} s"}
+
+    if rank == 0:
+        h2d = 2 * 3 * 8 * n_part
+        line = {
+            "metric": "particle-updates/s per full PM step at 512^3 (mixed precision)",
+            "value": value, "unit": "particle-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"relativistic PM step, {n}^3 mesh, {n}^3 particles, box {box:.0f} Mpc/h, "
+                                   f"LCDM Om={OM} h={H}, Zel'dovich/BBKS ICs z={ZI:.0f}, seed {SEED}, "
+                                   f"steps {args.warmup}..{args.warmup + args.steps - 1} of a "
+                                   f"{N_STEPS_SCHEDULE}-step schedule",
+                       "precision": "mixed: int32 cell + f32 offset, f32 fields/FFT, f64 background and k=0, "
+                                    "compensated cell sums",
+                       "components": "T00, 3 T0i, 5 trace-free Tij; phi, chi, B_i, h (2 helicities)",
+                       "parallelism": f"replicas x{world}", "l2": "working set ~25 GB >> 129 MB L2, no flush",
+                       "ic_seconds": round(t_ic, 1)},
+            "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
+            "kernels_roofline_frac": per_kernel_frac,
+            "step_roofline_frac": survey_bytes_per_update(True) * n_part / (ms_max * 1e-3) / 1e9 / peak,
+            "design_bytes_per_step": design_bytes,
+            "design_roofline_frac": design_bytes / (ms_max * 1e-3) / 1e9 / peak,
+            "roofline": roofline,
+            "fp64": fp64,
+            "e2e": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                    "how": "pm_put_particles(pinned host f64 pos, mom) + pm_step + pm_get_particles(pinned host)"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -90,9 +90,15 @@ enum {
 /* Tensor state ids for pm_get_tensor: helicity amplitudes and their tau derivatives. */
 enum { PM_TENSOR_HPLUS = 0, PM_TENSOR_HCROSS = 1, PM_TENSOR_DHPLUS = 2, PM_TENSOR_DHCROSS = 3 };
 
-/* Stage ids for pm_get_timings (milliseconds of the latest step, CUDA events). */
+/* Stage ids for pm_get_timings: mean milliseconds per step, from CUDA events
+ * recorded on cfg->stream around each kernel of every step.  Stages and
+ * kernels: projection (deposit + source assembly), forward FFT (x, y, z
+ * passes), Fourier solve, inverse FFT (z, y, x passes), gather + kick + drift,
+ * counting sort (scan, scatter), and the whole step. */
 enum { PM_T_PROJECT = 0, PM_T_FFT_FWD = 1, PM_T_SOLVE = 2, PM_T_FFT_INV = 3, PM_T_UPDATE = 4,
-       PM_T_SORT = 5, PM_T_STEP = 6, PM_T_COUNT = 7 };
+       PM_T_SORT = 5, PM_T_STEP = 6, PM_T_FFT_FWD_X = 7, PM_T_FFT_FWD_Y = 8, PM_T_FFT_FWD_Z = 9,
+       PM_T_FFT_INV_Z = 10, PM_T_FFT_INV_Y = 11, PM_T_FFT_INV_X = 12, PM_T_SCAN = 13,
+       PM_T_SCATTER = 14, PM_T_COUNT = 15 };
 
 /* Create a context: validates cfg, computes the FP64 background schedule
  * (Sec. 3.1: Hc = d ln a / d tau, flat LCDM; steps uniform in ln a from
@@ -140,6 +146,14 @@ pm_status pm_update(pm_ctx *ctx);
 /* pm_project + pm_solve + pm_update. */
 pm_status pm_step(pm_ctx *ctx);
 
+/* Replace the particle state between steps without touching the fields,
+ * the step index or the tensor state: pos, mom [n_part][3] f64 (host or
+ * device) as in pm_set_particles; ids are reassigned to the row order.
+ * Used to feed a running simulation from outside (e.g. host buffers every
+ * step).  Errors: INVALID_ARG (NULL, NaN/Inf), STATE (no particles yet or
+ * mid-step), CUDA. */
+pm_status pm_put_particles(pm_ctx *ctx, const double *pos, const double *mom);
+
 /* Current particle state in id order: pos [n_part][3] (box units, [0,1)),
  * mom [n_part][3] (u at half a step before the next step).  Either pointer
  * may be NULL to skip it.  Errors: INVALID_ARG, STATE, CUDA. */
@@ -169,8 +183,12 @@ pm_status pm_get_time(pm_ctx *ctx, int32_t *step, double *a, double *tau);
 /* Schedule arrays: a_n[n_steps+1], dtau[n_steps], a_half[n_steps] (host). */
 pm_status pm_get_schedule(pm_ctx *ctx, double *a_n, double *dtau, double *a_half);
 
-/* Stage timings of the latest step in ms (see PM_T_*), n <= PM_T_COUNT. */
-pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n);
+/* Mean stage timings in ms per step (see PM_T_*) over the steps completed
+ * since the previous call (at most the last 64), n <= PM_T_COUNT; stages
+ * without steps read 0.  Synchronises the stream, then starts a new window.
+ * *launches (may be NULL) receives the number of library kernels launched
+ * in that window. */
+pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n, int64_t *launches);
 
 /* Checkpoint: write / read the full state (config, step, particles,
  * phi_{n-1}, chi_{n-1}, phi_{n-2}, tensor state) to / from a host file.

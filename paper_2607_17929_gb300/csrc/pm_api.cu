@@ -173,10 +173,9 @@ template <class T> pm_status do_solve(Ctx &c, bool bootstrap)
     const int nf = full ? 9 : 1;
     fft_forward<T>(c, nf, sr, sp);
     CKL("fft_forward");
-    CK(cudaEventRecord(c.ev[2], c.stream));
     launch_solve<T>(c, s);
     CKL("solve");
-    CK(cudaEventRecord(c.ev[3], c.stream));
+    c.mark(EV_SOLVE);
     // phi_n, B_x, B_y, B_z, chi_n from spectra 0..4
     void *outs[5] = {c.phi[c.iphi_new], reinterpret_cast<T *>(c.B), reinterpret_cast<T *>(c.B) + c.nc,
                      reinterpret_cast<T *>(c.B) + 2 * c.nc, c.chi};
@@ -194,7 +193,7 @@ template <class T> pm_status do_update(Ctx &c)
     StepScalars s = scalars(c, c.step, false);
     launch_kick_drift<T>(c, s);
     CKL("kick_drift");
-    CK(cudaEventRecord(c.ev[5], c.stream));
+    c.mark(EV_KICK);
     launch_sort<T>(c);
     CKL("sort");
     return PM_OK;
@@ -209,10 +208,12 @@ void rotate(Ctx &c)
     c.iphi_new = old2;
 }
 
-template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const double *mom)
+template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const double *mom, bool bootstrap)
 {
-    c.have_particles = false;
-    c.stage = 0;
+    if (bootstrap) {
+        c.have_particles = false;
+        c.stage = 0;
+    }
     CK(cudaMemsetAsync(c.count, 0, sizeof(int32_t) * c.nc, c.stream));
     const bool dev = is_device_ptr(pos) && is_device_ptr(mom);
     int *dflag = reinterpret_cast<int *>(c.dscal + 4);
@@ -239,9 +240,13 @@ template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const do
     int hflag = 0;
     CK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
-    if (hflag) return fail(c, PM_ERR_INVALID_ARG, "pm_set_particles: non-finite position or momentum");
+    if (hflag) {
+        if (!bootstrap) c.have_particles = false;  // the previous state was overwritten
+        return fail(c, PM_ERR_INVALID_ARG, "non-finite position or momentum");
+    }
     launch_sort<T>(c);
     CKL("sort");
+    if (!bootstrap) return PM_OK;
     // bootstrap: phi_{-1} = chi_{-1} = 0 in the weights, quasi-static solve
     CK(cudaMemsetAsync(c.phi[c.iphi_prev], 0, sizeof(T) * c.nc, c.stream));
     CK(cudaMemsetAsync(c.chi, 0, sizeof(T) * c.nc, c.stream));
@@ -627,7 +632,8 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
     cudaMemset(c.B, 0, 3 * ts * c.nc);
     cudaMemset(c.tens, 0, 4 * 2 * ts * c.nh);
     cudaMemset(c.count, 0, sizeof(int32_t) * c.nc);
-    for (auto &e : c.ev) cudaEventCreate(&e);
+    for (auto &row : c.evr)
+        for (auto &e : row) cudaEventCreate(&e);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         pm_destroy(ctx);
@@ -648,8 +654,9 @@ void pm_destroy(pm_ctx *ctx)
                   c.src, c.spec, c.tens, c.ktab, c.tw, c.dscal, c.stage_buf};
     for (void *p : ps)
         if (p) cudaFree(p);
-    for (auto &e : c.ev)
-        if (e) cudaEventDestroy(e);
+    for (auto &row : c.evr)
+        for (auto &e : row)
+            if (e) cudaEventDestroy(e);
     cudaGetLastError();
     delete ctx;
 }
@@ -665,7 +672,17 @@ pm_status pm_set_particles(pm_ctx *ctx, const double *pos, const double *mom)
     if (g) return g;
     Ctx &c = ctx->c;
     if (!pos || !mom) return fail(c, PM_ERR_INVALID_ARG, "pm_set_particles: NULL array");
-    return PM_DISPATCH(ctx, set_particles_t, c, pos, mom);
+    return PM_DISPATCH(ctx, set_particles_t, c, pos, mom, true);
+}
+
+pm_status pm_put_particles(pm_ctx *ctx, const double *pos, const double *mom)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (!pos || !mom) return fail(c, PM_ERR_INVALID_ARG, "pm_put_particles: NULL array");
+    if (!c.have_particles || c.stage != 0) return fail(c, PM_ERR_STATE, "pm_put_particles: not between steps");
+    return PM_DISPATCH(ctx, set_particles_t, c, pos, mom, false);
 }
 
 pm_status pm_project(pm_ctx *ctx)
@@ -676,10 +693,13 @@ pm_status pm_project(pm_ctx *ctx)
     if (!c.have_particles) return fail(c, PM_ERR_STATE, "pm_project: no particles");
     if (c.step >= c.cfg.n_steps) return fail(c, PM_ERR_STATE, "pm_project: schedule exhausted");
     if (c.stage != 0) return fail(c, PM_ERR_STATE, "pm_project: previous step not finished");
-    cudaEventRecord(c.ev[0], c.stream);
+    c.stepc++;
+    c.timing_on = true;
+    c.mark(EV_START);
     pm_status st = PM_DISPATCH(ctx, do_project, c, false);
+    c.mark(EV_PROJECT);
+    c.timing_on = false;
     if (st) return st;
-    cudaEventRecord(c.ev[1], c.stream);
     c.stage = 1;
     return PM_OK;
 }
@@ -690,9 +710,10 @@ pm_status pm_solve(pm_ctx *ctx)
     if (g) return g;
     Ctx &c = ctx->c;
     if (c.stage != 1) return fail(c, PM_ERR_STATE, "pm_solve: call pm_project first");
+    c.timing_on = true;
     pm_status st = PM_DISPATCH(ctx, do_solve, c, false);
+    c.timing_on = false;
     if (st) return st;
-    cudaEventRecord(c.ev[4], c.stream);
     c.stage = 2;
     return PM_OK;
 }
@@ -703,9 +724,12 @@ pm_status pm_update(pm_ctx *ctx)
     if (g) return g;
     Ctx &c = ctx->c;
     if (c.stage != 2) return fail(c, PM_ERR_STATE, "pm_update: call pm_solve first");
+    c.timing_on = true;
     pm_status st = PM_DISPATCH(ctx, do_update, c);
+    c.mark(EV_END);
+    c.timing_on = false;
     if (st) return st;
-    cudaEventRecord(c.ev[6], c.stream);
+    c.window = std::min<int64_t>(c.window + 1, Ctx::RING);
     rotate(c);
     c.step += 1;
     c.stage = 0;
@@ -784,26 +808,35 @@ pm_status pm_get_schedule(pm_ctx *ctx, double *a_n, double *dtau, double *a_half
     return PM_OK;
 }
 
-pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n)
+pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n, int64_t *launches)
 {
     pm_status g = guard(ctx);
     if (g) return g;
     Ctx &c = ctx->c;
     if (!ms || n < 0 || n > PM_T_COUNT) return fail(c, PM_ERR_INVALID_ARG, "pm_get_timings: bad arguments");
-    cudaError_t e = cudaEventSynchronize(c.ev[6]);
+    cudaError_t e = c.stream ? cudaStreamSynchronize(c.stream) : cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "pm_get_timings");
-    float t[PM_T_COUNT] = {};
-    // project: ev0->ev1, fft fwd: ev1->ev2, solve: ev2->ev3, fft inv: ev3->ev4,
-    // kick+drift: ev4->ev5, sort: ev5->ev6, whole step: ev0->ev6
-    cudaEventElapsedTime(&t[PM_T_PROJECT], c.ev[0], c.ev[1]);
-    cudaEventElapsedTime(&t[PM_T_FFT_FWD], c.ev[1], c.ev[2]);
-    cudaEventElapsedTime(&t[PM_T_SOLVE], c.ev[2], c.ev[3]);
-    cudaEventElapsedTime(&t[PM_T_FFT_INV], c.ev[3], c.ev[4]);
-    cudaEventElapsedTime(&t[PM_T_UPDATE], c.ev[4], c.ev[5]);
-    cudaEventElapsedTime(&t[PM_T_SORT], c.ev[5], c.ev[6]);
-    cudaEventElapsedTime(&t[PM_T_STEP], c.ev[0], c.ev[6]);
+    // stage -> (first event, last event)
+    static const int span[PM_T_COUNT][2] = {
+        {EV_START, EV_PROJECT}, {EV_PROJECT, EV_FWD_Z}, {EV_FWD_Z, EV_SOLVE}, {EV_SOLVE, EV_INV_X},
+        {EV_INV_X, EV_KICK},    {EV_KICK, EV_END},      {EV_START, EV_END},   {EV_PROJECT, EV_FWD_X},
+        {EV_FWD_X, EV_FWD_Y},   {EV_FWD_Y, EV_FWD_Z},   {EV_SOLVE, EV_INV_Z}, {EV_INV_Z, EV_INV_Y},
+        {EV_INV_Y, EV_INV_X},   {EV_KICK, EV_SCAN},     {EV_SCAN, EV_END}};
+    double acc[PM_T_COUNT] = {};
+    const int64_t w = c.window;
+    for (int64_t k = 0; k < w; k++) {
+        const int64_t slot = (c.stepc - k) % Ctx::RING;
+        for (int t = 0; t < PM_T_COUNT; t++) {
+            float v = 0.f;
+            if (cudaEventElapsedTime(&v, c.evr[slot][span[t][0]], c.evr[slot][span[t][1]]) == cudaSuccess)
+                acc[t] += v;
+        }
+    }
     cudaGetLastError();
-    for (int i = 0; i < n; i++) ms[i] = t[i];
+    for (int t = 0; t < n; t++) ms[t] = w ? acc[t] / (double)w : 0.0;
+    if (launches) *launches = c.launches - c.launches_mark;
+    c.launches_mark = c.launches;
+    c.window = 0;
     return PM_OK;
 }
 

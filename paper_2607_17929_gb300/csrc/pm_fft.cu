@@ -313,6 +313,7 @@ void col_pass(Ctx &c, int nf, const Ptrs &p, int64_t stride_j, int64_t ncols, in
     k_fft_cols<T><<<grid, fft_block<T>(), cols_smem<T>(c.N, L), c.stream>>>(
         p, reinterpret_cast<const typename Cplx<T>::type *>(c.tw), c.plan, L, stride_j, ncols, stride_b, nlines,
         s);
+    c.launches++;
 }
 
 }  // namespace
@@ -334,10 +335,14 @@ void fft_forward(Ctx &c, int nf, const void *const *real_in, void *const *spec_o
     dim3 grid((unsigned)((npairs + L - 1) / L), nf);
     k_fft_r2c<T><<<grid, fft_block<T>(), cols_smem<T>(N, L), c.stream>>>(
         pi, po, reinterpret_cast<const typename Cplx<T>::type *>(c.tw), c.plan, L, npairs);
+    c.launches++;
+    c.mark(EV_FWD_X);
     // y: lines (z, kx), points stride h
     col_pass<T>(c, nf, po, h, h, (int64_t)N * h, (int64_t)N * h, -1);
+    c.mark(EV_FWD_Y);
     // z: lines (ky, kx), points stride N h
     col_pass<T>(c, nf, po, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, -1);
+    c.mark(EV_FWD_Z);
 }
 
 template <class T>
@@ -352,12 +357,16 @@ void fft_inverse(Ctx &c, int nf, void *const *spec_in, void *const *real_out)
         po.p[i] = real_out[i];
     }
     col_pass<T>(c, nf, pi, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, +1);
+    c.mark(EV_INV_Z);
     col_pass<T>(c, nf, pi, h, h, (int64_t)N * h, (int64_t)N * h, +1);
+    c.mark(EV_INV_Y);
     int L = lines_per_block<T>(N);
     int64_t npairs = (int64_t)N * N / 2;
     dim3 grid((unsigned)((npairs + L - 1) / L), nf);
     k_fft_c2r<T><<<grid, fft_block<T>(), cols_smem<T>(N, L), c.stream>>>(
         pi, po, reinterpret_cast<const typename Cplx<T>::type *>(c.tw), c.plan, L, npairs);
+    c.launches++;
+    c.mark(EV_INV_X);
 }
 
 template void fft_forward<double>(Ctx &, int, const void *const *, void *const *);

@@ -114,9 +114,24 @@ struct Ctx {
     int64_t stage_elems = 0;
     FftPlan plan;
 
-    cudaEvent_t ev[8] = {};
-    double t_ms[PM_T_COUNT] = {};
+    // per-kernel CUDA events of the last RING steps (timing window) and the
+    // number of library kernels launched
+    static constexpr int RING = 64, NEV = 12;
+    cudaEvent_t evr[RING][NEV] = {};
+    bool timing_on = false;   // marks are recorded only inside pm_project/solve/update
+    int64_t stepc = 0;        // steps started (selects the ring slot)
+    int64_t window = 0;       // completed steps in the current timing window
+    int64_t launches = 0, launches_mark = 0;
+
+    void mark(int point)
+    {
+        if (timing_on) cudaEventRecord(evr[stepc % RING][point], stream);
+    }
 };
+
+// Event points inside one step.
+enum { EV_START = 0, EV_PROJECT = 1, EV_FWD_X = 2, EV_FWD_Y = 3, EV_FWD_Z = 4, EV_SOLVE = 5,
+       EV_INV_Z = 6, EV_INV_Y = 7, EV_INV_X = 8, EV_KICK = 9, EV_SCAN = 10, EV_END = 11 };
 
 // ---------------------------------------------------------------------------
 // Launchers (implemented in pm_fft.cu, pm_particles.cu, pm_solve.cu).

@@ -691,6 +691,7 @@ void launch_project(Ctx &c, const StepScalars &s)
     const int ntiles = (c.N / TILE) * (c.N / TILE) * (c.N / TILE);
     k_project<T><<<ntiles, DEP_THREADS, dep_smem<T>(), c.stream>>>(p);
     k_k0_reduce<<<1, 1024, 0, c.stream>>>(c.dscal);
+    c.launches += 2;
 }
 
 template <class T>
@@ -716,6 +717,7 @@ void launch_kick_drift(Ctx &c, const StepScalars &s)
     p.dt_drift_N = (T)(s.dtau * c.N);
     p.halfN = (T)(0.5 * c.N);
     k_kick_drift<T><<<nblk(c.np, 256), 256, 0, c.stream>>>(p);
+    c.launches++;
 }
 
 void launch_scan(Ctx &c)
@@ -724,16 +726,19 @@ void launch_scan(Ctx &c)
     k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, c.stream>>>(c.count, c.nc, c.blocksum);
     k_scan_top<<<1, SCAN_T, 0, c.stream>>>(c.blocksum, nb, c.start + c.nc);
     k_scan_down<<<(unsigned)nb, SCAN_T, 0, c.stream>>>(c.count, c.nc, c.blocksum, c.start);
+    c.launches += 3;
 }
 
 template <class T>
 void launch_sort(Ctx &c)
 {
     launch_scan(c);
+    c.mark(EV_SCAN);
     const int o = 1 - c.cur;
     k_scatter<T><<<nblk(c.np, 256), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[c.cur]),
                                                          reinterpret_cast<Particle<T> *>(c.part[o]), c.np,
                                                          c.start, c.count);
+    c.launches++;
     c.cur = o;
 }
 

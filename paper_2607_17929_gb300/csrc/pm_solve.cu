@@ -227,6 +227,7 @@ void launch_solve(Ctx &c, const StepScalars &s)
     p.hc_half = (T)s.hc_half;
     p.dtau = (T)s.dtau;
     k_solve<T><<<(unsigned)((c.nh + 255) / 256), 256, 0, c.stream>>>(p);
+    c.launches++;
 }
 
 template <class T>

@@ -23,7 +23,8 @@ PM_NEWTONIAN = 1
 FIELDS = {"phi": 0, "chi": 1, "Bx": 2, "By": 3, "Bz": 4, "R": 5, "Fx": 6, "Fy": 7, "Fz": 8,
           "Sxx": 9, "Sxy": 10, "Sxz": 11, "Syy": 12, "Syz": 13}
 TENSORS = {"h+": 0, "hx": 1, "h+'": 2, "hx'": 3}
-TIMINGS = ["project", "fft_fwd", "solve", "fft_inv", "kick_drift", "sort", "step"]
+TIMINGS = ["project", "fft_fwd", "solve", "fft_inv", "kick_drift", "sort", "step", "fft_fwd_x", "fft_fwd_y",
+           "fft_fwd_z", "fft_inv_z", "fft_inv_y", "fft_inv_x", "scan", "scatter"]
 
 
 class pm_config(C.Structure):
@@ -60,7 +61,8 @@ def _load():
         "pm_power_spectrum": ([vp, C.c_int, dp, dp, C.POINTER(i64)], C.c_int),
         "pm_get_time": ([vp, C.POINTER(i32), dp, dp], C.c_int),
         "pm_get_schedule": ([vp, dp, dp, dp], C.c_int),
-        "pm_get_timings": ([vp, dp, C.c_int], C.c_int),
+        "pm_get_timings": ([vp, dp, C.c_int, C.POINTER(i64)], C.c_int),
+        "pm_put_particles": ([vp, vp, vp], C.c_int),
         "pm_save": ([vp, C.c_char_p], C.c_int),
         "pm_load": ([vp, C.c_char_p], C.c_int),
     }
@@ -74,7 +76,7 @@ def _load():
 lib = _load()
 
 EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_project", "pm_solve",
-            "pm_update", "pm_step", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
+            "pm_update", "pm_step", "pm_put_particles", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
             "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
 
 
@@ -141,6 +143,10 @@ def pm_step(ctx):
     _check(ctx, lib.pm_step(ctx))
 
 
+def pm_put_particles(ctx, pos, mom):
+    _check(ctx, lib.pm_put_particles(ctx, _ptr(pos), _ptr(mom)))
+
+
 def pm_get_particles(ctx, pos, mom):
     _check(ctx, lib.pm_get_particles(ctx, _ptr(pos), _ptr(mom)))
 
@@ -177,9 +183,11 @@ def pm_get_schedule(ctx, n_steps):
 
 
 def pm_get_timings(ctx):
+    """Mean per-kernel ms over the steps since the previous call, and the kernel launch count."""
     ms = np.zeros(len(TIMINGS))
-    _check(ctx, lib.pm_get_timings(ctx, ms.ctypes.data_as(C.POINTER(C.c_double)), len(TIMINGS)))
-    return dict(zip(TIMINGS, ms.tolist()))
+    nl = C.c_int64()
+    _check(ctx, lib.pm_get_timings(ctx, ms.ctypes.data_as(C.POINTER(C.c_double)), len(TIMINGS), C.byref(nl)))
+    return dict(zip(TIMINGS, ms.tolist())), nl.value
 
 
 def pm_save(ctx, path):
@@ -213,6 +221,9 @@ class PM:
 
     def set_particles(self, pos, mom):
         pm_set_particles(self.ctx, pos, mom)
+
+    def put_particles(self, pos, mom):
+        pm_put_particles(self.ctx, pos, mom)
 
     def step(self):
         pm_step(self.ctx)

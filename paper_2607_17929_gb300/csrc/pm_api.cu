@@ -589,6 +589,7 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
         {&c.tens, 4 * 2 * ts * (size_t)c.nh},
         {&c.ktab, ts * (size_t)c.N},
         {&c.tw, 2 * ts * (size_t)c.N},
+        {&c.tw2, 2 * ts * (size_t)(2 * c.N + 64)},
         {(void **)&c.dscal, sizeof(double) * (8 + 1024)},
         {&c.stage_buf, sizeof(double) * (size_t)c.stage_elems},
     };
@@ -608,6 +609,15 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
             kt[i] = (double)(2.0L * c.N * sinl(pi * m / c.N));
             tw[2 * i] = (double)cosl(2.0L * pi * i / c.N);
             tw[2 * i + 1] = (double)(-sinl(2.0L * pi * i / c.N));
+        }
+        std::vector<double> tw2;
+        fast_twiddles(c.N, tw2);
+        if (tw2.size() > 2 * (size_t)(2 * c.N + 64)) tw2.resize(2 * (size_t)(2 * c.N + 64));
+        if (c.mixed) {
+            std::vector<float> tw2f(tw2.begin(), tw2.end());
+            if (!tw2f.empty()) cudaMemcpy(c.tw2, tw2f.data(), sizeof(float) * tw2f.size(), cudaMemcpyHostToDevice);
+        } else if (!tw2.empty()) {
+            cudaMemcpy(c.tw2, tw2.data(), sizeof(double) * tw2.size(), cudaMemcpyHostToDevice);
         }
         if (c.mixed) {
             std::vector<float> ktf(kt.begin(), kt.end()), twf(tw.begin(), tw.end());
@@ -651,7 +661,7 @@ void pm_destroy(pm_ctx *ctx)
     if (c.stream) cudaStreamSynchronize(c.stream);
     else cudaDeviceSynchronize();
     void *ps[] = {c.part[0], c.part[1], c.count, c.start, c.blocksum, c.phi[0], c.phi[1], c.phi[2], c.chi, c.B,
-                  c.src, c.spec, c.tens, c.ktab, c.tw, c.dscal, c.stage_buf};
+                  c.src, c.spec, c.tens, c.ktab, c.tw, c.tw2, c.dscal, c.stage_buf};
     for (void *p : ps)
         if (p) cudaFree(p);
     for (auto &row : c.evr)

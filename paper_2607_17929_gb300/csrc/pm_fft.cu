@@ -12,6 +12,7 @@
 // complex values per row: 128-byte segments), runs a Stockham autosort
 // FFT (Govindaraju et al., SC'08 formulation) with radices 8, 4, 2 and 3
 // in registers, and writes the lines back.
+#include "pm_fft_core.cuh"
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -316,6 +317,195 @@ void col_pass(Ctx &c, int nf, const Ptrs &p, int64_t stride_j, int64_t ncols, in
     c.launches++;
 }
 
+
+// ---------------------------------------------------------------------------
+// Compile-time-N passes (register-resident radix stages, see pm_fft_core.cuh).
+// ---------------------------------------------------------------------------
+template <class T, int N> struct Lines {
+    static constexpr int TL = fftc::Geo<N>::TL;
+    static constexpr int col0 = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int col1 = col0 * TL < 128 ? 128 / TL : col0;
+    static constexpr int col = col1 * TL > 1024 ? 1024 / TL : col1;   // lines per block, column passes
+    static constexpr int row = TL >= 256 ? 1 : 256 / TL;               // row pairs per block, x passes
+};
+
+template <class T, int N> size_t col_fast_smem()
+{
+    using G = fftc::Geo<N>;
+    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)N * (Lines<T, N>::col + 1));
+}
+template <class T, int N> size_t row_fast_smem()
+{
+    using G = fftc::Geo<N>;
+    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)Lines<T, N>::row * fftc::RowIdx<N>::pitch);
+}
+
+template <class T, int N, int DIR>
+__global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::col)
+k_col_fast(Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t stride_j, int64_t ncols,
+           int64_t stride_b, int64_t nlines)
+{
+    using C = typename Cplx<T>::type;
+    using G = fftc::Geo<N>;
+    constexpr int L = Lines<T, N>::col;
+    extern __shared__ __align__(16) unsigned char smem[];
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf = tw + G::TWN;
+    for (int i = threadIdx.x; i < G::TWN; i += blockDim.x) tw[i] = twg[i];
+    const int l = threadIdx.x % L, t = threadIdx.x / L;
+    const int64_t g = (int64_t)blockIdx.x * L + l;
+    const bool ok = g < nlines;
+    const int64_t base = ok ? (g / ncols) * stride_b + (g % ncols) : 0;
+    C *data = reinterpret_cast<C *>(ptrs.p[blockIdx.y]);
+    C v[G::P];
+#pragma unroll
+    for (int i = 0; i < G::P; i++)
+        v[i] = ok ? data[base + (int64_t)fftc::in_pos<N>(t, i) * stride_j] : fftc::mk<C>(0, 0);
+    __syncthreads();
+    fftc::fft<C, N, DIR>(v, t, buf, tw, fftc::ColIdx{L + 1, l});
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < G::P; i++) data[base + (int64_t)fftc::out_pos<N>(t, i) * stride_j] = v[i];
+    }
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::row)
+k_r2c_fast(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, int64_t npairs)
+{
+    using C = typename Cplx<T>::type;
+    using G = fftc::Geo<N>;
+    constexpr int L = Lines<T, N>::row, H = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf = tw + G::TWN;
+    for (int i = threadIdx.x; i < G::TWN; i += blockDim.x) tw[i] = twg[i];
+    const int t = threadIdx.x % G::TL, l = threadIdx.x / G::TL;
+    const int64_t pair = (int64_t)blockIdx.x * L + l;
+    const bool ok = pair < npairs;
+    const T *src = reinterpret_cast<const T *>(in.p[blockIdx.y]);
+    C *dst = reinterpret_cast<C *>(out.p[blockIdx.y]);
+    const T *ra = src + 2 * pair * N, *rb = ra + N;
+    C v[G::P];
+#pragma unroll
+    for (int i = 0; i < G::P; i++) {
+        const int j = fftc::in_pos<N>(t, i);
+        v[i] = ok ? fftc::mk<C>(ra[j], rb[j]) : fftc::mk<C>(0, 0);
+    }
+    __syncthreads();
+    const fftc::RowIdx<N> ix{l * fftc::RowIdx<N>::pitch};
+    fftc::fft<C, N, -1>(v, t, buf, tw, ix);
+#pragma unroll
+    for (int i = 0; i < G::P; i++) buf[ix(fftc::out_pos<N>(t, i))] = v[i];
+    __syncthreads();
+    if (!ok) return;
+    C *oa = dst + 2 * pair * H, *ob = oa + H;
+    const T half = (T)0.5;
+    for (int k = t; k < H; k += G::TL) {
+        const C zk = buf[ix(k)], zn = buf[ix((N - k) % N)];
+        oa[k] = fftc::mk<C>(half * (zk.x + zn.x), half * (zk.y - zn.y));
+        ob[k] = fftc::mk<C>(half * (zk.y + zn.y), -half * (zk.x - zn.x));
+    }
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::row)
+k_c2r_fast(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, int64_t npairs)
+{
+    using C = typename Cplx<T>::type;
+    using G = fftc::Geo<N>;
+    constexpr int L = Lines<T, N>::row, H = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    C *tw = reinterpret_cast<C *>(smem);
+    C *buf = tw + G::TWN;
+    for (int i = threadIdx.x; i < G::TWN; i += blockDim.x) tw[i] = twg[i];
+    const int t = threadIdx.x % G::TL, l = threadIdx.x / G::TL;
+    const int64_t pair = (int64_t)blockIdx.x * L + l;
+    const bool ok = pair < npairs;
+    const C *src = reinterpret_cast<const C *>(in.p[blockIdx.y]);
+    T *dst = reinterpret_cast<T *>(out.p[blockIdx.y]);
+    const fftc::RowIdx<N> ix{l * fftc::RowIdx<N>::pitch};
+    const C *ia = src + 2 * pair * H, *ib = ia + H;
+    for (int k = t; k < H; k += G::TL) {
+        C A = fftc::mk<C>(0, 0), B = fftc::mk<C>(0, 0);
+        if (ok) {
+            A = ia[k];
+            B = ib[k];
+        }
+        if (k == 0 || 2 * k == N) {
+            A.y = 0;
+            B.y = 0;
+        }
+        buf[ix(k)] = fftc::mk<C>(A.x - B.y, A.y + B.x);
+        if (k > 0 && 2 * k < N) buf[ix(N - k)] = fftc::mk<C>(A.x + B.y, B.x - A.y);
+    }
+    __syncthreads();
+    C v[G::P];
+#pragma unroll
+    for (int i = 0; i < G::P; i++) v[i] = buf[ix(fftc::in_pos<N>(t, i))];
+    __syncthreads();
+    fftc::fft<C, N, +1>(v, t, buf, tw, ix);
+    if (!ok) return;
+    T *wa = dst + 2 * pair * N, *wb = wa + N;
+#pragma unroll
+    for (int i = 0; i < G::P; i++) {
+        const int j = fftc::out_pos<N>(t, i);
+        wa[j] = v[i].x;
+        wb[j] = v[i].y;
+    }
+}
+
+template <class T, int N> struct FastPasses {
+    static void attrs()
+    {
+        static bool done = false;
+        if (done) return;
+        done = true;
+        cudaFuncSetAttribute(k_col_fast<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_fast_smem<T, N>());
+        cudaFuncSetAttribute(k_col_fast<T, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_fast_smem<T, N>());
+        cudaFuncSetAttribute(k_r2c_fast<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fast_smem<T, N>());
+        cudaFuncSetAttribute(k_c2r_fast<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fast_smem<T, N>());
+    }
+    static void cols(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    {
+        constexpr int L = Lines<T, N>::col;
+        dim3 grid((unsigned)((nl + L - 1) / L), nf);
+        const auto *tw = reinterpret_cast<const typename Cplx<T>::type *>(c.tw2);
+        if (dir < 0)
+            k_col_fast<T, N, -1><<<grid, fftc::Geo<N>::TL * L, col_fast_smem<T, N>(), c.stream>>>(p, tw, sj, nc, sb, nl);
+        else
+            k_col_fast<T, N, 1><<<grid, fftc::Geo<N>::TL * L, col_fast_smem<T, N>(), c.stream>>>(p, tw, sj, nc, sb, nl);
+        c.launches++;
+    }
+    static void rows(Ctx &c, int nf, const Ptrs &pi, const Ptrs &po, int dir)
+    {
+        constexpr int L = Lines<T, N>::row;
+        const int64_t npairs = (int64_t)N * N / 2;
+        dim3 grid((unsigned)((npairs + L - 1) / L), nf);
+        const auto *tw = reinterpret_cast<const typename Cplx<T>::type *>(c.tw2);
+        if (dir < 0)
+            k_r2c_fast<T, N><<<grid, fftc::Geo<N>::TL * L, row_fast_smem<T, N>(), c.stream>>>(pi, po, tw, npairs);
+        else
+            k_c2r_fast<T, N><<<grid, fftc::Geo<N>::TL * L, row_fast_smem<T, N>(), c.stream>>>(pi, po, tw, npairs);
+        c.launches++;
+    }
+};
+
+// calls f.template operator()<N>() for the specialised sizes; false otherwise
+template <class F> bool with_fast_n(int n, F &&f)
+{
+    switch (n) {
+    case 16: f.template operator()<16>(); return true;
+    case 32: f.template operator()<32>(); return true;
+    case 64: f.template operator()<64>(); return true;
+    case 128: f.template operator()<128>(); return true;
+    case 192: f.template operator()<192>(); return true;
+    case 256: f.template operator()<256>(); return true;
+    case 512: f.template operator()<512>(); return true;
+    default: return false;
+    }
+}
+
 }  // namespace
 
 template <class T>
@@ -329,6 +519,17 @@ void fft_forward(Ctx &c, int nf, const void *const *real_in, void *const *spec_o
         pi.p[i] = const_cast<void *>(real_in[i]);
         po.p[i] = spec_out[i];
     }
+    auto fast = [&]<int NN>() {
+        using F = FastPasses<T, NN>;
+        F::attrs();
+        F::rows(c, nf, pi, po, -1);
+        c.mark(EV_FWD_X);
+        F::cols(c, nf, po, h, h, (int64_t)N * h, (int64_t)N * h, -1);
+        c.mark(EV_FWD_Y);
+        F::cols(c, nf, po, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, -1);
+        c.mark(EV_FWD_Z);
+    };
+    if (with_fast_n(N, fast)) return;
     // x: real rows -> half-spectrum rows.  L complex lines = L row pairs per block.
     int L = lines_per_block<T>(N);
     int64_t npairs = (int64_t)N * N / 2;
@@ -356,6 +557,17 @@ void fft_inverse(Ctx &c, int nf, void *const *spec_in, void *const *real_out)
         pi.p[i] = spec_in[i];
         po.p[i] = real_out[i];
     }
+    auto fast = [&]<int NN>() {
+        using F = FastPasses<T, NN>;
+        F::attrs();
+        F::cols(c, nf, pi, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, +1);
+        c.mark(EV_INV_Z);
+        F::cols(c, nf, pi, h, h, (int64_t)N * h, (int64_t)N * h, +1);
+        c.mark(EV_INV_Y);
+        F::rows(c, nf, pi, po, +1);
+        c.mark(EV_INV_X);
+    };
+    if (with_fast_n(N, fast)) return;
     col_pass<T>(c, nf, pi, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, +1);
     c.mark(EV_INV_Z);
     col_pass<T>(c, nf, pi, h, h, (int64_t)N * h, (int64_t)N * h, +1);
@@ -367,6 +579,26 @@ void fft_inverse(Ctx &c, int nf, void *const *spec_in, void *const *real_out)
         pi, po, reinterpret_cast<const typename Cplx<T>::type *>(c.tw), c.plan, L, npairs);
     c.launches++;
     c.mark(EV_INV_X);
+}
+
+bool fast_fft_supported(int n)
+{
+    return with_fast_n(n, []<int NN>() {});
+}
+
+void fast_twiddles(int n, std::vector<double> &re_im)
+{
+    re_im.clear();
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int s = 1; s < fftc::nstages(n); s++) {
+        const int Ns = fftc::span_before(n, s), R = fftc::radix_at(n, s);
+        for (int k = 0; k < Ns; k++)
+            for (int r = 1; r < R; r++) {
+                const long double ang = -2.0L * pi * (long double)(r * k) / (long double)(Ns * R);
+                re_im.push_back((double)cosl(ang));
+                re_im.push_back((double)sinl(ang));
+            }
+    }
 }
 
 template void fft_forward<double>(Ctx &, int, const void *const *, void *const *);

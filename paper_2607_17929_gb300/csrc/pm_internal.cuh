@@ -109,6 +109,7 @@ struct Ctx {
     void *tens = nullptr;       // 4 * nh complex tensor state
     void *ktab = nullptr;       // N values of ktilde(n)
     void *tw = nullptr;         // N twiddles exp(-2 pi i k / N)
+    void *tw2 = nullptr;        // per-stage twiddles of the compile-time-N passes
     double *dscal = nullptr;    // device f64 scalars: [0] k=0 particle sum, [1] mean phi_{n-1}, [2] mean phi_n
     void *stage_buf = nullptr;  // host-transfer staging (f64)
     int64_t stage_elems = 0;
@@ -167,5 +168,9 @@ template <class T>
 void launch_check_finite(Ctx &c, const double *d, int64_t n, int *d_flag);
 
 void launch_scan(Ctx &c);
+
+// compile-time-N FFT passes (pm_fft.cu)
+bool fast_fft_supported(int n);
+void fast_twiddles(int n, std::vector<double> &re_im);
 
 }  // namespace pm

@@ -93,11 +93,12 @@ def test_fp64_ten_steps_32cubed(pm):
 
 
 @pytest.mark.parametrize("n,n_side,box,newtonian", [(24, 20, 240.0, False), (16, 7, 160.0, False),
-                                                    (24, 21, 240.0, True), (48, 30, 480.0, False)])
+                                                    (24, 21, 240.0, True), (48, 30, 480.0, False),
+                                                    (64, 40, 640.0, False), (128, 50, 1000.0, True)])
 def test_fp64_ragged_and_radix3(pm, n, n_side, box, newtonian):
     """Mesh sizes with a factor 3, particle counts that are not n^3, sparse loads, Newtonian mode."""
     orc, g, *_ = make_pair(pm, n, n_side, box, 5, pm.PM_FP64, newtonian=newtonian)
-    for _ in range(3):
+    for _ in range(3 if n <= 48 else 2):
         orc.step()
         g.step()
     e = compare(orc, g, n, full=not newtonian)

@@ -173,7 +173,7 @@ template <class T> constexpr int fft_block() { return sizeof(T) == 8 ? 256 : 512
 // data[b * stride_b + j * stride_j + c].
 template <class T>
 __global__ void __launch_bounds__(fft_block<T>())
-k_fft_cols(Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t stride_j,
+k_fft_cols(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t stride_j,
            int64_t ncols, int64_t stride_b, int64_t nlines, int s)
 {
     using C = typename Cplx<T>::type;
@@ -210,7 +210,7 @@ k_fft_cols(Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, FftPlan pl
 // FFT, then A_k = (Z_k + conj Z_{N-k})/2, B_k = -i (Z_k - conj Z_{N-k})/2.
 template <class T>
 __global__ void __launch_bounds__(fft_block<T>())
-k_fft_r2c(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t npairs)
+k_fft_r2c(const __grid_constant__ Ptrs in, const __grid_constant__ Ptrs out, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t npairs)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -250,7 +250,7 @@ k_fft_r2c(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, Fft
 // dropped), inverse FFT, a = Re z, b = Im z.
 template <class T>
 __global__ void __launch_bounds__(fft_block<T>())
-k_fft_c2r(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t npairs)
+k_fft_c2r(const __grid_constant__ Ptrs in, const __grid_constant__ Ptrs out, const typename Cplx<T>::type *__restrict__ twg, FftPlan plan, int L, int64_t npairs)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -323,10 +323,13 @@ void col_pass(Ctx &c, int nf, const Ptrs &p, int64_t stride_j, int64_t ncols, in
 // ---------------------------------------------------------------------------
 template <class T, int N> struct Lines {
     static constexpr int TL = fftc::Geo<N>::TL;
-    static constexpr int col0 = sizeof(T) == 4 ? 16 : 8;
+    // lines per block of the column passes: 64-byte row segments, at least 128 threads
+    static constexpr int col0 = sizeof(T) == 4 ? 8 : 4;
     static constexpr int col1 = col0 * TL < 128 ? 128 / TL : col0;
-    static constexpr int col = col1 * TL > 1024 ? 1024 / TL : col1;   // lines per block, column passes
+    static constexpr int col = col1 * TL > 512 ? 512 / TL : col1;
     static constexpr int row = TL >= 256 ? 1 : 256 / TL;               // row pairs per block, x passes
+    // resident blocks per SM the register allocation must allow (P = 8 sizes)
+    static constexpr int col_min_blocks = fftc::Geo<N>::P == 8 ? (sizeof(T) == 4 ? 1536 / (TL * col) : 1024 / (TL * col)) : 1;
 };
 
 template <class T, int N> size_t col_fast_smem()
@@ -341,8 +344,8 @@ template <class T, int N> size_t row_fast_smem()
 }
 
 template <class T, int N, int DIR>
-__global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::col)
-k_col_fast(Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t stride_j, int64_t ncols,
+__global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::col, Lines<T, N>::col_min_blocks)
+k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t stride_j, int64_t ncols,
            int64_t stride_b, int64_t nlines)
 {
     using C = typename Cplx<T>::type;
@@ -371,7 +374,7 @@ k_col_fast(Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t st
 
 template <class T, int N>
 __global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::row)
-k_r2c_fast(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, int64_t npairs)
+k_r2c_fast(const __grid_constant__ Ptrs in, const __grid_constant__ Ptrs out, const typename Cplx<T>::type *__restrict__ twg, int64_t npairs)
 {
     using C = typename Cplx<T>::type;
     using G = fftc::Geo<N>;
@@ -410,7 +413,7 @@ k_r2c_fast(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, in
 
 template <class T, int N>
 __global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::row)
-k_c2r_fast(Ptrs in, Ptrs out, const typename Cplx<T>::type *__restrict__ twg, int64_t npairs)
+k_c2r_fast(const __grid_constant__ Ptrs in, const __grid_constant__ Ptrs out, const typename Cplx<T>::type *__restrict__ twg, int64_t npairs)
 {
     using C = typename Cplx<T>::type;
     using G = fftc::Geo<N>;

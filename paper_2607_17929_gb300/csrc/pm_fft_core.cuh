@@ -93,7 +93,7 @@ template <int S, class C> struct Dft<3, S, C> {
 };
 
 // ---- compile-time plan: radix 3 stages first, then 8s, then a 4 or 2 -----
-constexpr int radix_at(int n, int s)
+__host__ __device__ constexpr int radix_at(int n, int s)
 {
     int m = n, st = 0;
     while (m % 3 == 0) {
@@ -118,20 +118,20 @@ constexpr int radix_at(int n, int s)
     }
     return 0;
 }
-constexpr int nstages(int n)
+__host__ __device__ constexpr int nstages(int n)
 {
     int s = 0;
     while (radix_at(n, s)) s++;
     return s;
 }
-constexpr int span_before(int n, int s)
+__host__ __device__ constexpr int span_before(int n, int s)
 {
     int p = 1;
     for (int i = 0; i < s; i++) p *= radix_at(n, i);
     return p;
 }
 // offset of stage s in the per-stage twiddle table ([k][r-1] per stage, s >= 1)
-constexpr int tw_offset(int n, int s)
+__host__ __device__ constexpr int tw_offset(int n, int s)
 {
     int o = 0;
     for (int i = 1; i < s; i++) o += span_before(n, i) * (radix_at(n, i) - 1);

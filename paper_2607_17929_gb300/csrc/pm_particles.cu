@@ -23,8 +23,10 @@ constexpr int NFLD = FLD * FLD * FLD;  // 1000
 constexpr int DEP_THREADS = TILE * TILE * TILE;  // 512
 constexpr int NK0SLOTS = 1024;
 
-// Per-cell accumulator.  FP64: plain double.  Mixed: float-float with
-// Knuth's TwoSum, so a cell sum keeps about 48 significant bits.
+// Per-cell accumulator of the T^00 charge, whose cell sums cancel against the
+// uniform background in R.  FP64: plain double.  Mixed: float-float with
+// Knuth's TwoSum, so a cell sum keeps about 48 significant bits.  The other
+// components have no such cancellation and are summed in the field type.
 template <class T> struct Acc;
 template <> struct Acc<double> {
     double s;
@@ -76,13 +78,19 @@ template <class T> struct DepParams {
 
 template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 1536; }
 
-static_assert((sizeof(double) * (2 * NFLD + 12 * 640)) % 8 == 0 && (sizeof(float) * (2 * NFLD + 12 * 1536)) % 8 == 0,
-              "shared-memory T arrays must end on an 8-byte boundary");
-
 template <class T> size_t dep_smem()
 {
-    return sizeof(T) * (2 * NFLD + 12 * dep_cap<T>()) + sizeof(int) * (3 * NREG + 64) + sizeof(double) * 32;
+    return sizeof(T) * (12 * dep_cap<T>() + 2 * NFLD) + sizeof(double) * 32 + sizeof(int) * (3 * NREG + 64);
 }
+
+// Per-particle record in shared memory: {fx, fy, fz, q00}, {q0x, q0y, q0z, Txx}, {Txy, Txz, Tyy, Tyz}
+// (trace-free T_ij, Tzz implied), read back with three 16-byte (FP32) or six 16-byte (FP64) loads.
+template <class T> struct alignas(16) DepRec {
+    T f[3], q00, q0[3], txx, txy, txz, tyy, tyz;
+};
+static_assert(sizeof(DepRec<float>) == 48 && sizeof(DepRec<double>) == 96, "packed record");
+// 2 * NFLD field values keep the following f64 scratch 8-byte aligned
+static_assert((sizeof(float) * 2 * NFLD) % 8 == 0, "alignment");
 
 // Exclusive scan of v[0..n) (n <= 2 * blockDim) in place; returns the total.
 __device__ int block_exclusive_scan(int *v, int n, int *warp_tmp)
@@ -119,20 +127,18 @@ __device__ int block_exclusive_scan(int *v, int n, int *warp_tmp)
 }
 
 template <class T>
-__global__ void __launch_bounds__(DEP_THREADS) k_project(DepParams<T> p)
+__global__ void __launch_bounds__(DEP_THREADS) k_project(const __grid_constant__ DepParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int CAP = dep_cap<T>();
-    T *sphi = reinterpret_cast<T *>(smem);
+    DepRec<T> *rec = reinterpret_cast<DepRec<T> *>(smem);            // [CAP]
+    T *sphi = reinterpret_cast<T *>(rec + CAP);
     T *schi = sphi + NFLD;
-    T *sq = schi + NFLD;          // [9][CAP] charges
-    T *sf = sq + 9 * CAP;         // [3][CAP] offsets
-    // the T arrays span a multiple of 8 bytes, so the f64 scratch stays aligned
-    double *sred = reinterpret_cast<double *>(sf + 3 * CAP);  // 32 doubles
+    double *sred = reinterpret_cast<double *>(schi + NFLD);          // 32 doubles
     int *scnt = reinterpret_cast<int *>(sred + 32);
     int *soff = scnt + NREG;
     int *sgs = soff + NREG;
-    int *wtmp = sgs + NREG;       // 64 ints
+    int *wtmp = sgs + NREG;                                          // 64 ints
 
     const int N = p.N, nt = p.nt, tid = threadIdx.x;
     const int b = blockIdx.x;
@@ -158,11 +164,11 @@ __global__ void __launch_bounds__(DEP_THREADS) k_project(DepParams<T> p)
     const int total = block_exclusive_scan(soff, NREG, wtmp);
 
     const int ox = tid % TILE, oy = (tid / TILE) % TILE, oz = tid / (TILE * TILE);
-    Acc<T> acc[9];
-#pragma unroll
-    for (int c = 0; c < 9; c++) acc[c].zero();
+    Acc<T> acc00;
+    acc00.zero();
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double k0 = 0.0;
-    const int ncomp = p.full ? 9 : 1;
+    const bool full = p.full;
 
     for (int lo = 0; lo < total; lo += CAP) {
         const int hi = min(total, lo + CAP);
@@ -177,77 +183,82 @@ __global__ void __launch_bounds__(DEP_THREADS) k_project(DepParams<T> p)
             const int t = t0;
             const Particle<T> P = p.part[sgs[t] + (i - soff[t])];
             const int sx = t % REG, sy = (t / REG) % REG, sz = t / (REG * REG);
-            const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
-            const int j = i - lo;
-            sf[j] = fx;
-            sf[CAP + j] = fy;
-            sf[2 * CAP + j] = fz;
-            if (!p.full && p.newtonian) {
-                sq[j] = p.mass;
-                continue;
-            }
-            T ph = 0, ch = 0;
-            if (p.use_fields) {
-                const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+            DepRec<T> r;
+            r.f[0] = P.f[0];
+            r.f[1] = P.f[1];
+            r.f[2] = P.f[2];
+            if (!full && p.newtonian) {
+                r.q00 = p.mass;
+            } else {
+                T ph = 0, ch = 0;
+                if (p.use_fields) {
+                    const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
+                    const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
 #pragma unroll
-                for (int dz = 0; dz < 2; dz++)
+                    for (int dz = 0; dz < 2; dz++)
 #pragma unroll
-                    for (int dy = 0; dy < 2; dy++)
+                        for (int dy = 0; dy < 2; dy++)
 #pragma unroll
-                        for (int dx = 0; dx < 2; dx++) {
-                            const T w = wx[dx] * wy[dy] * wz[dz];
-                            const int v = (sx + dx) + FLD * ((sy + dy) + FLD * (sz + dz));
-                            ph += w * sphi[v];
-                            ch += w * schi[v];
-                        }
+                            for (int dx = 0; dx < 2; dx++) {
+                                const T w = wx[dx] * wy[dy] * wz[dz];
+                                const int v = (sx + dx) + FLD * ((sy + dy) + FLD * (sz + dz));
+                                ph += w * sphi[v];
+                                ch += w * schi[v];
+                            }
+                }
+                const T ux = P.u[0], uy = P.u[1], uz = P.u[2];
+                const T u2 = ux * ux + uy * uy + uz * uz;
+                const T E = sqrt(p.a2 + u2);
+                const T iE = T(1) / E;
+                const T v2 = u2 * iE * iE;
+                const T m = p.mass;
+                // T^00 charge and its excess over a particle at rest (k = 0 mode in FP64)
+                r.q00 = m * E * (T(1) + T(3) * ph + ph * v2);
+                if (sx >= 1 && sy >= 1 && sz >= 1) k0 += (double)(m * (u2 / (E + p.a) + E * (T(3) * ph + ph * v2)));
+                if (full) {
+                    const T wv = m * (T(1) + T(4) * ph - ch);
+                    r.q0[0] = wv * ux;
+                    r.q0[1] = wv * uy;
+                    r.q0[2] = wv * uz;
+                    const T ws = m * (T(1) + T(3) * ph - ph * v2) * iE;
+                    const T txx = ws * ux * ux, tyy = ws * uy * uy, tzz = ws * uz * uz;
+                    const T tr3 = (txx + tyy + tzz) * T(1.0 / 3.0);
+                    r.txx = txx - tr3;
+                    r.txy = ws * ux * uy;
+                    r.txz = ws * ux * uz;
+                    r.tyy = tyy - tr3;
+                    r.tyz = ws * uy * uz;
+                }
             }
-            const T ux = P.u[0], uy = P.u[1], uz = P.u[2];
-            const T u2 = ux * ux + uy * uy + uz * uz;
-            const T E = sqrt(p.a2 + u2);
-            const T iE = T(1) / E;
-            const T v2 = u2 * iE * iE;
-            const T m = p.mass;
-            // T^00 charge and its excess over a particle at rest (k = 0 mode in FP64)
-            sq[j] = m * E * (T(1) + T(3) * ph + ph * v2);
-            if (sx >= 1 && sy >= 1 && sz >= 1) {
-                const T excess = m * (u2 / (E + p.a) + E * (T(3) * ph + ph * v2));
-                k0 += (double)excess;
-            }
-            if (p.full) {
-                const T wv = m * (T(1) + T(4) * ph - ch);
-                sq[CAP + j] = wv * ux;
-                sq[2 * CAP + j] = wv * uy;
-                sq[3 * CAP + j] = wv * uz;
-                const T ws = m * (T(1) + T(3) * ph - ph * v2) * iE;
-                const T txx = ws * ux * ux, tyy = ws * uy * uy, tzz = ws * uz * uz;
-                const T tr3 = (txx + tyy + tzz) * T(1.0 / 3.0);
-                sq[4 * CAP + j] = txx - tr3;
-                sq[5 * CAP + j] = ws * ux * uy;
-                sq[6 * CAP + j] = ws * ux * uz;
-                sq[7 * CAP + j] = tyy - tr3;
-                sq[8 * CAP + j] = ws * uy * uz;
-            }
+            rec[i - lo] = r;
         }
         __syncthreads();
-        // vertex (ox, oy, oz) receives from source cells (o - d), d in {0,1}^3,
-        // with weight (d ? f : 1 - f) per axis
+        // vertex o receives from source cells o - d, d in {0,1}^3, weight (d ? f : 1 - f) per axis.
+        // The two x-neighbours (region x = ox and ox + 1) are adjacent in the particle order.
 #pragma unroll
         for (int dz = 0; dz < 2; dz++)
 #pragma unroll
-            for (int dy = 0; dy < 2; dy++)
-#pragma unroll
-                for (int dx = 0; dx < 2; dx++) {
-                    const int ts = (ox + 1 - dx) + REG * ((oy + 1 - dy) + REG * (oz + 1 - dz));
-                    const int jb = max(soff[ts], lo), je = min(soff[ts] + scnt[ts], hi);
-                    for (int jj = jb; jj < je; jj++) {
-                        const int j = jj - lo;
-                        const T gx = sf[j], gy = sf[CAP + j], gz = sf[2 * CAP + j];
-                        const T w = (dx ? gx : T(1) - gx) * (dy ? gy : T(1) - gy) * (dz ? gz : T(1) - gz);
-#pragma unroll
-                        for (int c = 0; c < 9; c++)
-                            if (c < ncomp) acc[c].add(mulr(w, sq[c * CAP + j]));
+            for (int dy = 0; dy < 2; dy++) {
+                const int ts = ox + REG * ((oy + 1 - dy) + REG * (oz + 1 - dz));  // cell with dx = 1
+                const int mid = soff[ts + 1];                                     // first particle with dx = 0
+                const int jb = max(soff[ts], lo), je = min(mid + scnt[ts + 1], hi);
+                for (int jj = jb; jj < je; jj++) {
+                    const DepRec<T> r = rec[jj - lo];
+                    const T wyz = (dy ? r.f[1] : T(1) - r.f[1]) * (dz ? r.f[2] : T(1) - r.f[2]);
+                    const T w = (jj < mid ? r.f[0] : T(1) - r.f[0]) * wyz;
+                    acc00.add(mulr(w, r.q00));
+                    if (full) {
+                        acc[0] += w * r.q0[0];
+                        acc[1] += w * r.q0[1];
+                        acc[2] += w * r.q0[2];
+                        acc[3] += w * r.txx;
+                        acc[4] += w * r.txy;
+                        acc[5] += w * r.txz;
+                        acc[6] += w * r.tyy;
+                        acc[7] += w * r.tyz;
                     }
                 }
+            }
         __syncthreads();
     }
 
@@ -271,9 +282,9 @@ __global__ void __launch_bounds__(DEP_THREADS) k_project(DepParams<T> p)
     const int vo = (ox + 1) + FLD * ((oy + 1) + FLD * (oz + 1));
     const T phc = sphi[vo], chc = schi[vo];
     // R: the uniform background a*Omega_m is removed before rounding
-    const T dS = (acc[0].hi() - p.rb_hi) + (acc[0].lo() - p.rb_lo);
+    const T dS = (acc00.hi() - p.rb_hi) + (acc00.lo() - p.rb_lo);
     reinterpret_cast<T *>(p.out.p[0])[go] = p.G * dS - p.c1 * phc - p.c2 * chc;
-    if (!p.full) return;
+    if (!full) return;
     T gphi[3], gpsi[3];
     const int st[3] = {1, FLD, FLD * FLD};
 #pragma unroll
@@ -285,8 +296,7 @@ __global__ void __launch_bounds__(DEP_THREADS) k_project(DepParams<T> p)
     }
     const T dphi = (phc - p.phi2[go]) * p.inv_dt2;
 #pragma unroll
-    for (int d = 0; d < 3; d++)
-        reinterpret_cast<T *>(p.out.p[1 + d])[go] = p.G * (acc[1 + d].hi() + acc[1 + d].lo()) - dphi * gpsi[d];
+    for (int d = 0; d < 3; d++) reinterpret_cast<T *>(p.out.p[1 + d])[go] = p.G * acc[d] - dphi * gpsi[d];
     T Q[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -294,16 +304,11 @@ __global__ void __launch_bounds__(DEP_THREADS) k_project(DepParams<T> p)
         for (int j = 0; j < 3; j++) Q[i][j] = T(2) * gphi[i] * gphi[j] - (gphi[i] + gpsi[i]) * (gphi[j] + gpsi[j]);
     const T trQ3 = (Q[0][0] + Q[1][1] + Q[2][2]) * T(1.0 / 3.0);
     const T G4 = T(4) * p.G;
-    const T Sxx = G4 * (acc[4].hi() + acc[4].lo()) - T(2) * (Q[0][0] - trQ3);
-    const T Sxy = G4 * (acc[5].hi() + acc[5].lo()) - T(2) * Q[0][1];
-    const T Sxz = G4 * (acc[6].hi() + acc[6].lo()) - T(2) * Q[0][2];
-    const T Syy = G4 * (acc[7].hi() + acc[7].lo()) - T(2) * (Q[1][1] - trQ3);
-    const T Syz = G4 * (acc[8].hi() + acc[8].lo()) - T(2) * Q[1][2];
-    reinterpret_cast<T *>(p.out.p[4])[go] = Sxx;
-    reinterpret_cast<T *>(p.out.p[5])[go] = Sxy;
-    reinterpret_cast<T *>(p.out.p[6])[go] = Sxz;
-    reinterpret_cast<T *>(p.out.p[7])[go] = Syy;
-    reinterpret_cast<T *>(p.out.p[8])[go] = Syz;
+    reinterpret_cast<T *>(p.out.p[4])[go] = G4 * acc[3] - T(2) * (Q[0][0] - trQ3);
+    reinterpret_cast<T *>(p.out.p[5])[go] = G4 * acc[4] - T(2) * Q[0][1];
+    reinterpret_cast<T *>(p.out.p[6])[go] = G4 * acc[5] - T(2) * Q[0][2];
+    reinterpret_cast<T *>(p.out.p[7])[go] = G4 * acc[6] - T(2) * (Q[1][1] - trQ3);
+    reinterpret_cast<T *>(p.out.p[8])[go] = G4 * acc[7] - T(2) * Q[1][2];
 }
 
 // Sum the k = 0 slots: dscal[0] = sum over particles of the T^00 excess.
@@ -334,113 +339,165 @@ __global__ void k_k0_reduce(double *dscal)
 // ---------------------------------------------------------------------------
 template <class T> struct KdParams {
     Particle<T> *part;
+    const int32_t *start;
     int32_t *count;
     const T *phi, *chi, *Bx, *By, *Bz;
     int64_t np;
-    int N;
+    int N, nt;
     int newtonian;
     T a, a2, a_half2, inv_a_half, dt_kick, dt_drift_N, halfN;
 };
 
+constexpr int KT = 8;                     // tile side in cells
+constexpr int KV = KT + 3;                // vertices per axis: x0-1 .. x0+9
+constexpr int KNV = KV * KV * KV;         // 1331
+constexpr int KD_THREADS = 256;
+
+template <class T> size_t kd_smem() { return sizeof(T) * 5 * KNV + sizeof(int) * (2 * KT * KT + 2 + 33); }
+
+// One CTA per 8^3 tile of cells: phi, chi and B on the 11^3 vertices around
+// the tile go to shared memory once; each thread then gathers the CIC value
+// and centred-difference gradients for one particle from there.
 template <class T>
-__global__ void __launch_bounds__(256) k_kick_drift(KdParams<T> p)
+__global__ void __launch_bounds__(KD_THREADS) k_kick_drift(KdParams<T> p)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.np) return;
-    Particle<T> P = p.part[i];
-    const int N = p.N;
-    const int ix = P.cell % N, iy = (P.cell / N) % N, iz = P.cell / (N * N);
-    const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
-    int xs[4], ys[4], zs[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        xs[k] = wrapi(ix - 1 + k, N);
-        ys[k] = wrapi(iy - 1 + k, N);
-        zs[k] = wrapi(iz - 1 + k, N);
-    }
-    // value weights W(0) = 1-f, W(1) = f; gradient weights over offsets -1..2
-    const T hn = p.halfN;
-    const T Wx[4] = {0, T(1) - fx, fx, 0}, Wy[4] = {0, T(1) - fy, fy, 0}, Wz[4] = {0, T(1) - fz, fz, 0};
-    const T Gx[4] = {-(T(1) - fx) * hn, -fx * hn, (T(1) - fx) * hn, fx * hn};
-    const T Gy[4] = {-(T(1) - fy) * hn, -fy * hn, (T(1) - fy) * hn, fy * hn};
-    const T Gz[4] = {-(T(1) - fz) * hn, -fz * hn, (T(1) - fz) * hn, fz * hn};
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sf = reinterpret_cast<T *>(smem);                 // [5][KNV]
+    int *roff = reinterpret_cast<int *>(sf + 5 * KNV);   // 65 row offsets (+1 pad)
+    int *rgs = roff + KT * KT + 2;                        // 64 global row starts
+    int *wtmp = rgs + KT * KT;                            // 33
+    const int N = p.N, nt = p.nt, tid = threadIdx.x;
+    const int b = blockIdx.x;
+    const int x0 = (b % nt) * KT, y0 = ((b / nt) % nt) * KT, z0 = (b / (nt * nt)) * KT;
     const int nf = p.newtonian ? 1 : 5;
     const T *F[5] = {p.phi, p.chi, p.Bx, p.By, p.Bz};
-    T val[5] = {0, 0, 0, 0, 0};
-    T grd[5][3] = {};
+
+    // particle rows of the tile: cells (x0 .. x0+7, y, z) are contiguous
+    int cnt = 0;
+    if (tid < KT * KT) {
+        const int ry = tid % KT, rz = tid / KT;
+        const int64_t c0 = ((int64_t)(z0 + rz) * N + (y0 + ry)) * N + x0;
+        const int gs = p.start[c0];
+        cnt = p.start[c0 + KT] - gs;
+        rgs[tid] = gs;
+    }
+    // exclusive scan of the 64 row counts (two warps)
+    {
+        const int lane = tid & 31, wid = tid >> 5;
+        int x = cnt;
 #pragma unroll
-    for (int kz = 0; kz < 4; kz++)
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (wid < 2 && lane == 31) wtmp[wid] = x;
+        __syncthreads();
+        if (tid < KT * KT) roff[tid] = x - cnt + (wid == 1 ? wtmp[0] : 0);
+        if (tid == 0) roff[KT * KT] = wtmp[0] + wtmp[1];
+    }
+    // fields on the vertex block
+    for (int i = tid; i < KNV; i += KD_THREADS) {
+        const int rx = i % KV, ry = (i / KV) % KV, rz = i / (KV * KV);
+        const int64_t g = ((int64_t)wrapi(z0 - 1 + rz, N) * N + wrapi(y0 - 1 + ry, N)) * N + wrapi(x0 - 1 + rx, N);
 #pragma unroll
-        for (int ky = 0; ky < 4; ky++)
+        for (int q = 0; q < 5; q++)
+            if (q < nf) sf[q * KNV + i] = __ldg(F[q] + g);
+    }
+    __syncthreads();
+    const int total = roff[KT * KT];
+    const T hn = p.halfN;
+    for (int i = tid; i < total; i += KD_THREADS) {
+        int r0 = 0, r1 = KT * KT - 1;
+        while (r0 < r1) {
+            const int m = (r0 + r1 + 1) >> 1;
+            if (roff[m] <= i) r0 = m;
+            else r1 = m - 1;
+        }
+        const int64_t gi = (int64_t)rgs[r0] + (i - roff[r0]);
+        Particle<T> P = p.part[gi];
+        const int ix = P.cell % N, iy = (P.cell / N) % N, iz = P.cell / (N * N);
+        const int lx = ix - x0, ly = iy - y0, lz = iz - z0;   // 0..7; vertex block index of offset -1
+        const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
+        const T Wx[4] = {0, T(1) - fx, fx, 0}, Wy[4] = {0, T(1) - fy, fy, 0}, Wz[4] = {0, T(1) - fz, fz, 0};
+        const T Gx[4] = {-(T(1) - fx) * hn, -fx * hn, (T(1) - fx) * hn, fx * hn};
+        const T Gy[4] = {-(T(1) - fy) * hn, -fy * hn, (T(1) - fy) * hn, fy * hn};
+        const T Gz[4] = {-(T(1) - fz) * hn, -fz * hn, (T(1) - fz) * hn, fz * hn};
+        const int vb = lx + KV * (ly + KV * lz);
+        T val[5] = {0, 0, 0, 0, 0};
+        T grd[5][3] = {};
 #pragma unroll
-            for (int kx = 0; kx < 4; kx++) {
-                const bool cx = (kx == 1 || kx == 2), cy = (ky == 1 || ky == 2), cz = (kz == 1 || kz == 2);
-                if ((int)!cx + (int)!cy + (int)!cz > 1) continue;
-                const T wv = Wx[kx] * Wy[ky] * Wz[kz];
-                const T wgx = (cy && cz) ? Gx[kx] * Wy[ky] * Wz[kz] : T(0);
-                const T wgy = (cx && cz) ? Wx[kx] * Gy[ky] * Wz[kz] : T(0);
-                const T wgz = (cx && cy) ? Wx[kx] * Wy[ky] * Gz[kz] : T(0);
-                const int64_t g = ((int64_t)zs[kz] * N + ys[ky]) * N + xs[kx];
+        for (int kz = 0; kz < 4; kz++)
 #pragma unroll
-                for (int q = 0; q < 5; q++) {
-                    if (q >= nf) break;
-                    const T v = __ldg(F[q] + g);
-                    val[q] += wv * v;
-                    grd[q][0] += wgx * v;
-                    grd[q][1] += wgy * v;
-                    grd[q][2] += wgz * v;
+            for (int ky = 0; ky < 4; ky++)
+#pragma unroll
+                for (int kx = 0; kx < 4; kx++) {
+                    const bool cx = (kx == 1 || kx == 2), cy = (ky == 1 || ky == 2), cz = (kz == 1 || kz == 2);
+                    if ((int)!cx + (int)!cy + (int)!cz > 1) continue;
+                    const T wv = Wx[kx] * Wy[ky] * Wz[kz];
+                    const T wgx = (cy && cz) ? Gx[kx] * Wy[ky] * Wz[kz] : T(0);
+                    const T wgy = (cx && cz) ? Wx[kx] * Gy[ky] * Wz[kz] : T(0);
+                    const T wgz = (cx && cy) ? Wx[kx] * Wy[ky] * Gz[kz] : T(0);
+                    const int v = vb + kx + KV * (ky + KV * kz);
+#pragma unroll
+                    for (int q = 0; q < 5; q++) {
+                        if (q >= nf) break;
+                        const T s = sf[q * KNV + v];
+                        val[q] += wv * s;
+                        grd[q][0] += wgx * s;
+                        grd[q][1] += wgy * s;
+                        grd[q][2] += wgz * s;
+                    }
                 }
+        T u[3] = {P.u[0], P.u[1], P.u[2]};
+        T dx[3];
+        if (p.newtonian) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) u[d] -= p.dt_kick * p.a * grd[0][d];
+#pragma unroll
+            for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * u[d] * p.inv_a_half;
+        } else {
+            const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const T E = sqrt(p.a2 + u2);
+            const T u2E = u2 / E;
+            T K[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const T dpsi = grd[0][d] - grd[1][d];
+                K[d] = -E * dpsi - u2E * grd[0][d] - (u[0] * grd[2][d] + u[1] * grd[3][d] + u[2] * grd[4][d]);
             }
-    T u[3] = {P.u[0], P.u[1], P.u[2]};
-    T dx[3];
-    if (p.newtonian) {
 #pragma unroll
-        for (int d = 0; d < 3; d++) u[d] -= p.dt_kick * p.a * grd[0][d];
+            for (int d = 0; d < 3; d++) u[d] += p.dt_kick * K[d];
+            const T v2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const T Ed = sqrt(p.a_half2 + v2);
+            const T iEd = T(1) / Ed;
+            const T fac = (T(1) + T(3) * val[0] - val[1] - val[0] * v2 * iEd * iEd) * iEd;
 #pragma unroll
-        for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * u[d] * p.inv_a_half;
-    } else {
-        const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const T E = sqrt(p.a2 + u2);
-        const T u2E = u2 / E;
-        T K[3];
+            for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * (u[d] * fac + val[2 + d]);
+        }
+        const T fo[3] = {fx, fy, fz};
+        const int io[3] = {ix, iy, iz};
+        int inew[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const T dpsi = grd[0][d] - grd[1][d];
-            K[d] = -E * dpsi - u2E * grd[0][d] - (u[0] * grd[2][d] + u[1] * grd[3][d] + u[2] * grd[4][d]);
+            T f = fo[d] + dx[d];
+            T fl = floor(f);
+            f -= fl;
+            // a finite move is far below N cells; anything else (NaN, Inf) keeps the cell
+            int carry = (fabs(fl) < (T)N) ? (int)fl : 0;
+            if (f >= T(1)) {
+                f = T(0);
+                carry += 1;
+            }
+            int c = (io[d] + carry) % N;
+            if (c < 0) c += N;
+            inew[d] = c;
+            P.f[d] = f;
+            P.u[d] = u[d];
         }
-#pragma unroll
-        for (int d = 0; d < 3; d++) u[d] += p.dt_kick * K[d];
-        const T v2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const T Ed = sqrt(p.a_half2 + v2);
-        const T iEd = T(1) / Ed;
-        const T fac = (T(1) + T(3) * val[0] - val[1] - val[0] * v2 * iEd * iEd) * iEd;
-#pragma unroll
-        for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * (u[d] * fac + val[2 + d]);
+        P.cell = (inew[2] * N + inew[1]) * N + inew[0];
+        p.part[gi] = P;
+        atomicAdd(&p.count[P.cell], 1);
     }
-    // new offsets and cell (periodic), cell units
-    const T fo[3] = {fx, fy, fz};
-    const int io[3] = {ix, iy, iz};
-    int inew[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        T f = fo[d] + dx[d];
-        T fl = floor(f);
-        f -= fl;
-        // a finite move is far below N cells; anything else (NaN, Inf) keeps the cell
-        int carry = (fabs(fl) < (T)N) ? (int)fl : 0;
-        if (f >= T(1)) {
-            f = T(0);
-            carry += 1;
-        }
-        int c = (io[d] + carry) % N;
-        if (c < 0) c += N;
-        inew[d] = c;
-        P.f[d] = f;
-        P.u[d] = u[d];
-    }
-    P.cell = (inew[2] * N + inew[1]) * N + inew[0];
-    p.part[i] = P;
-    atomicAdd(&p.count[P.cell], 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -697,9 +754,16 @@ void launch_project(Ctx &c, const StepScalars &s)
 template <class T>
 void launch_kick_drift(Ctx &c, const StepScalars &s)
 {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_kick_drift<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kd_smem<T>());
+        attr = true;
+    }
     KdParams<T> p{};
     p.part = reinterpret_cast<Particle<T> *>(c.part[c.cur]);
+    p.start = c.start;
     p.count = c.count;
+    p.nt = c.N / KT;
     const T *B = reinterpret_cast<const T *>(c.B);
     p.phi = reinterpret_cast<const T *>(c.phi[c.iphi_new]);
     p.chi = reinterpret_cast<const T *>(c.chi);
@@ -716,7 +780,8 @@ void launch_kick_drift(Ctx &c, const StepScalars &s)
     p.dt_kick = (T)s.dtau_kick;
     p.dt_drift_N = (T)(s.dtau * c.N);
     p.halfN = (T)(0.5 * c.N);
-    k_kick_drift<T><<<nblk(c.np, 256), 256, 0, c.stream>>>(p);
+    const int ntiles = (c.N / KT) * (c.N / KT) * (c.N / KT);
+    k_kick_drift<T><<<ntiles, KD_THREADS, kd_smem<T>(), c.stream>>>(p);
     c.launches++;
 }
 

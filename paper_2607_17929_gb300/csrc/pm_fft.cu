@@ -335,7 +335,7 @@ template <class T, int N> struct Lines {
 template <class T, int N> size_t col_fast_smem()
 {
     using G = fftc::Geo<N>;
-    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)N * (Lines<T, N>::col + 1));
+    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)N * Lines<T, N>::col);
 }
 template <class T, int N> size_t row_fast_smem()
 {
@@ -365,7 +365,7 @@ k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__re
     for (int i = 0; i < G::P; i++)
         v[i] = ok ? data[base + (int64_t)fftc::in_pos<N>(t, i) * stride_j] : fftc::mk<C>(0, 0);
     __syncthreads();
-    fftc::fft<C, N, DIR>(v, t, buf, tw, fftc::ColIdx{L + 1, l});
+    fftc::fft<C, N, DIR>(v, t, buf, tw, fftc::ColIdx{L, l});
     if (ok) {
 #pragma unroll
         for (int i = 0; i < G::P; i++) data[base + (int64_t)fftc::out_pos<N>(t, i) * stride_j] = v[i];

@@ -221,11 +221,15 @@ __device__ __forceinline__ void fft(C (&v)[Geo<N>::P], int t, C *sm, const C *tw
     run_from<C, N, 0, DIR>(v, t, sm, tw, sidx);
 }
 
-// Shared-memory index maps.  Column kernels store [j][line] with an odd line
-// pitch; row kernels store [line][j] with one pad element every 8.
+// Shared-memory index maps.  Column kernels store [j][line] with the row
+// index swizzled by j ^ ((j >> 3) & 1): with 16-word rows (8 FP32 or 4 FP64
+// complex lines) consecutive rows and rows 8 apart fall in different bank
+// halves, so both the unit-stride reads and the stride-R first-stage writes
+// of a warp take the minimum two wavefronts.  Row kernels store [line][j]
+// with one pad element every 8.
 struct ColIdx {
     int pitch, l;
-    __device__ __forceinline__ int operator()(int j) const { return j * pitch + l; }
+    __device__ __forceinline__ int operator()(int j) const { return (j ^ ((j >> 3) & 1)) * pitch + l; }
 };
 template <int N> struct RowIdx {
     int base;

@@ -76,11 +76,12 @@ template <class T> struct DepParams {
     T halfN;         // N/2 (centred difference 1/(2 dx))
 };
 
-template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 1536; }
+template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 1024; }
 
 template <class T> size_t dep_smem()
 {
-    return sizeof(T) * (12 * dep_cap<T>() + 2 * NFLD) + sizeof(double) * 32 + sizeof(int) * (3 * NREG + 64);
+    return sizeof(T) * (12 * dep_cap<T>() + 2 * NFLD) + sizeof(double) * 32 +
+           sizeof(int) * (3 * NREG + 64 + FLD * FLD + FLD);
 }
 
 // Per-particle record in shared memory: {fx, fy, fz, q00}, {q0x, q0y, q0z, Txx}, {Txy, Txz, Tyy, Tyz}
@@ -127,7 +128,7 @@ __device__ int block_exclusive_scan(int *v, int n, int *warp_tmp)
 }
 
 template <class T>
-__global__ void __launch_bounds__(DEP_THREADS) k_project(const __grid_constant__ DepParams<T> p)
+__global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project(const __grid_constant__ DepParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int CAP = dep_cap<T>();
@@ -139,22 +140,38 @@ __global__ void __launch_bounds__(DEP_THREADS) k_project(const __grid_constant__
     int *soff = scnt + NREG;
     int *sgs = soff + NREG;
     int *wtmp = sgs + NREG;                                          // 64 ints
+    int *rowb = wtmp + 64;                                           // [FLD*FLD] wrapped (z,y) row bases
+    int *xw = rowb + FLD * FLD;                                      // [FLD] wrapped x
 
     const int N = p.N, nt = p.nt, tid = threadIdx.x;
     const int b = blockIdx.x;
     const int x0 = (b % nt) * TILE, y0 = ((b / nt) % nt) * TILE, z0 = (b / (nt * nt)) * TILE;
+    if (tid < FLD * FLD) {
+        const int ry = tid % FLD, rz = tid / FLD;
+        rowb[tid] = (wrapi(z0 - 1 + rz, N) * N + wrapi(y0 - 1 + ry, N)) * N;
+    }
+    if (tid < FLD) xw[tid] = wrapi(x0 - 1 + tid, N);
+    __syncthreads();
 
     // potentials of the previous solve on the 10^3 vertices [x0-1, x0+8]
-    for (int i = tid; i < NFLD; i += DEP_THREADS) {
-        int rx = i % FLD, ry = (i / FLD) % FLD, rz = i / (FLD * FLD);
-        int64_t g = ((int64_t)wrapi(z0 - 1 + rz, N) * N + wrapi(y0 - 1 + ry, N)) * N + wrapi(x0 - 1 + rx, N);
-        sphi[i] = p.use_fields ? p.phi1[g] : T(0);
-        schi[i] = p.use_fields ? p.chi1[g] : T(0);
+    if (p.use_fields) {
+        for (int i = tid; i < NFLD; i += DEP_THREADS) {
+            const int row = i / FLD, rx = i - row * FLD;
+            const int64_t g = (int64_t)rowb[row] + xw[rx];
+            sphi[i] = p.phi1[g];
+            schi[i] = p.chi1[g];
+        }
+    } else {
+        for (int i = tid; i < NFLD; i += DEP_THREADS) {
+            sphi[i] = T(0);
+            schi[i] = T(0);
+        }
     }
     // particle ranges of the 9^3 source cells [x0-1, x0+8)
     for (int i = tid; i < NREG; i += DEP_THREADS) {
-        int sx = i % REG, sy = (i / REG) % REG, sz = i / (REG * REG);
-        int64_t g = ((int64_t)wrapi(z0 - 1 + sz, N) * N + wrapi(y0 - 1 + sy, N)) * N + wrapi(x0 - 1 + sx, N);
+        const int row = i / REG, sx = i - row * REG;
+        const int sy = row % REG, sz = row / REG;
+        const int64_t g = (int64_t)rowb[sy + FLD * sz] + xw[sx];
         int gs = p.start[g];
         scnt[i] = p.start[g + 1] - gs;
         soff[i] = scnt[i];
@@ -353,25 +370,79 @@ constexpr int KV = KT + 3;                // vertices per axis: x0-1 .. x0+9
 constexpr int KNV = KV * KV * KV;         // 1331
 constexpr int KD_THREADS = 256;
 
-template <class T> size_t kd_smem() { return sizeof(T) * 5 * KNV + sizeof(int) * (2 * KT * KT + 2 + 33); }
+// phi, chi, B_x, B_y of one vertex in one 16-byte (FP32) or two 16-byte (FP64) loads
+template <class T> struct alignas(4 * sizeof(T) >= 16 ? 16 : 4 * sizeof(T)) Vtx4 {
+    T phi, chi, bx, by;
+};
+
+template <class T> size_t kd_smem()
+{
+    return sizeof(Vtx4<T>) * KNV + sizeof(T) * KNV + sizeof(int) * (KV * KV + KV + 2 * KT * KT + 2 + 33);
+}
+
+// Accumulate CIC value and centred-difference gradients of one vertex value s
+// at stencil offset (kx, ky, kz) in {0..3}^3 (offset -1 .. +2 from the cell);
+// terms whose weight is identically zero are skipped at compile time.
+template <int kx, int ky, int kz, class T>
+__device__ __forceinline__ void stencil_acc(T s, const T *Wx, const T *Wy, const T *Wz, const T *Gx, const T *Gy,
+                                            const T *Gz, T &val, T (&g)[3])
+{
+    constexpr bool cx = (kx == 1 || kx == 2), cy = (ky == 1 || ky == 2), cz = (kz == 1 || kz == 2);
+    if constexpr (cx && cy && cz) val += Wx[kx] * Wy[ky] * Wz[kz] * s;
+    if constexpr (cy && cz) g[0] += Gx[kx] * (Wy[ky] * Wz[kz]) * s;
+    if constexpr (cx && cz) g[1] += Gy[ky] * (Wx[kx] * Wz[kz]) * s;
+    if constexpr (cx && cy) g[2] += Gz[kz] * (Wx[kx] * Wy[ky]) * s;
+}
+
+template <int I, class T>
+__device__ __forceinline__ void gather_all(const Vtx4<T> *sv, const T *sbz, int vb, bool newtonian, const T *Wx,
+                                           const T *Wy, const T *Wz, const T *Gx, const T *Gy, const T *Gz, T (&val)[5],
+                                           T (&grd)[5][3])
+{
+    if constexpr (I < 64) {
+        constexpr int kx = I % 4, ky = (I / 4) % 4, kz = I / 16;
+        constexpr bool cx = (kx == 1 || kx == 2), cy = (ky == 1 || ky == 2), cz = (kz == 1 || kz == 2);
+        if constexpr ((int)!cx + (int)!cy + (int)!cz <= 1) {
+            const int v = vb + kx + KV * (ky + KV * kz);
+            if (newtonian) {
+                stencil_acc<kx, ky, kz>(sv[v].phi, Wx, Wy, Wz, Gx, Gy, Gz, val[0], grd[0]);
+            } else {
+                const Vtx4<T> a = sv[v];
+                const T bz = sbz[v];
+                stencil_acc<kx, ky, kz>(a.phi, Wx, Wy, Wz, Gx, Gy, Gz, val[0], grd[0]);
+                stencil_acc<kx, ky, kz>(a.chi, Wx, Wy, Wz, Gx, Gy, Gz, val[1], grd[1]);
+                stencil_acc<kx, ky, kz>(a.bx, Wx, Wy, Wz, Gx, Gy, Gz, val[2], grd[2]);
+                stencil_acc<kx, ky, kz>(a.by, Wx, Wy, Wz, Gx, Gy, Gz, val[3], grd[3]);
+                stencil_acc<kx, ky, kz>(bz, Wx, Wy, Wz, Gx, Gy, Gz, val[4], grd[4]);
+            }
+        }
+        gather_all<I + 1>(sv, sbz, vb, newtonian, Wx, Wy, Wz, Gx, Gy, Gz, val, grd);
+    }
+}
 
 // One CTA per 8^3 tile of cells: phi, chi and B on the 11^3 vertices around
 // the tile go to shared memory once; each thread then gathers the CIC value
 // and centred-difference gradients for one particle from there.
 template <class T>
-__global__ void __launch_bounds__(KD_THREADS) k_kick_drift(KdParams<T> p)
+__global__ void __launch_bounds__(KD_THREADS) k_kick_drift(const __grid_constant__ KdParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *sf = reinterpret_cast<T *>(smem);                 // [5][KNV]
-    int *roff = reinterpret_cast<int *>(sf + 5 * KNV);   // 65 row offsets (+1 pad)
-    int *rgs = roff + KT * KT + 2;                        // 64 global row starts
-    int *wtmp = rgs + KT * KT;                            // 33
+    Vtx4<T> *sv = reinterpret_cast<Vtx4<T> *>(smem);              // [KNV]
+    T *sbz = reinterpret_cast<T *>(sv + KNV);                      // [KNV]
+    int *rowb = reinterpret_cast<int *>(sbz + KNV);                // [KV*KV] wrapped (z,y) row bases
+    int *xw = rowb + KV * KV;                                      // [KV] wrapped x
+    int *roff = xw + KV;                                           // 65 row offsets (+1 pad)
+    int *rgs = roff + KT * KT + 2;                                 // 64 global row starts
+    int *wtmp = rgs + KT * KT;                                     // 33
     const int N = p.N, nt = p.nt, tid = threadIdx.x;
     const int b = blockIdx.x;
     const int x0 = (b % nt) * KT, y0 = ((b / nt) % nt) * KT, z0 = (b / (nt * nt)) * KT;
-    const int nf = p.newtonian ? 1 : 5;
-    const T *F[5] = {p.phi, p.chi, p.Bx, p.By, p.Bz};
 
+    if (tid < KV * KV) {
+        const int ry = tid % KV, rz = tid / KV;
+        rowb[tid] = (wrapi(z0 - 1 + rz, N) * N + wrapi(y0 - 1 + ry, N)) * N;
+    }
+    if (tid < KV) xw[tid] = wrapi(x0 - 1 + tid, N);
     // particle rows of the tile: cells (x0 .. x0+7, y, z) are contiguous
     int cnt = 0;
     if (tid < KT * KT) {
@@ -381,7 +452,6 @@ __global__ void __launch_bounds__(KD_THREADS) k_kick_drift(KdParams<T> p)
         cnt = p.start[c0 + KT] - gs;
         rgs[tid] = gs;
     }
-    // exclusive scan of the 64 row counts (two warps)
     {
         const int lane = tid & 31, wid = tid >> 5;
         int x = cnt;
@@ -397,11 +467,17 @@ __global__ void __launch_bounds__(KD_THREADS) k_kick_drift(KdParams<T> p)
     }
     // fields on the vertex block
     for (int i = tid; i < KNV; i += KD_THREADS) {
-        const int rx = i % KV, ry = (i / KV) % KV, rz = i / (KV * KV);
-        const int64_t g = ((int64_t)wrapi(z0 - 1 + rz, N) * N + wrapi(y0 - 1 + ry, N)) * N + wrapi(x0 - 1 + rx, N);
-#pragma unroll
-        for (int q = 0; q < 5; q++)
-            if (q < nf) sf[q * KNV + i] = __ldg(F[q] + g);
+        const int row = i / KV, rx = i - row * KV;
+        const int64_t g = (int64_t)rowb[row] + xw[rx];
+        Vtx4<T> a;
+        a.phi = __ldg(p.phi + g);
+        if (!p.newtonian) {
+            a.chi = __ldg(p.chi + g);
+            a.bx = __ldg(p.Bx + g);
+            a.by = __ldg(p.By + g);
+            sbz[i] = __ldg(p.Bz + g);
+        }
+        sv[i] = a;
     }
     __syncthreads();
     const int total = roff[KT * KT];
@@ -416,38 +492,15 @@ __global__ void __launch_bounds__(KD_THREADS) k_kick_drift(KdParams<T> p)
         const int64_t gi = (int64_t)rgs[r0] + (i - roff[r0]);
         Particle<T> P = p.part[gi];
         const int ix = P.cell % N, iy = (P.cell / N) % N, iz = P.cell / (N * N);
-        const int lx = ix - x0, ly = iy - y0, lz = iz - z0;   // 0..7; vertex block index of offset -1
+        const int vb = (ix - x0) + KV * ((iy - y0) + KV * (iz - z0));  // vertex block index of offset -1
         const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
         const T Wx[4] = {0, T(1) - fx, fx, 0}, Wy[4] = {0, T(1) - fy, fy, 0}, Wz[4] = {0, T(1) - fz, fz, 0};
         const T Gx[4] = {-(T(1) - fx) * hn, -fx * hn, (T(1) - fx) * hn, fx * hn};
         const T Gy[4] = {-(T(1) - fy) * hn, -fy * hn, (T(1) - fy) * hn, fy * hn};
         const T Gz[4] = {-(T(1) - fz) * hn, -fz * hn, (T(1) - fz) * hn, fz * hn};
-        const int vb = lx + KV * (ly + KV * lz);
         T val[5] = {0, 0, 0, 0, 0};
         T grd[5][3] = {};
-#pragma unroll
-        for (int kz = 0; kz < 4; kz++)
-#pragma unroll
-            for (int ky = 0; ky < 4; ky++)
-#pragma unroll
-                for (int kx = 0; kx < 4; kx++) {
-                    const bool cx = (kx == 1 || kx == 2), cy = (ky == 1 || ky == 2), cz = (kz == 1 || kz == 2);
-                    if ((int)!cx + (int)!cy + (int)!cz > 1) continue;
-                    const T wv = Wx[kx] * Wy[ky] * Wz[kz];
-                    const T wgx = (cy && cz) ? Gx[kx] * Wy[ky] * Wz[kz] : T(0);
-                    const T wgy = (cx && cz) ? Wx[kx] * Gy[ky] * Wz[kz] : T(0);
-                    const T wgz = (cx && cy) ? Wx[kx] * Wy[ky] * Gz[kz] : T(0);
-                    const int v = vb + kx + KV * (ky + KV * kz);
-#pragma unroll
-                    for (int q = 0; q < 5; q++) {
-                        if (q >= nf) break;
-                        const T s = sf[q * KNV + v];
-                        val[q] += wv * s;
-                        grd[q][0] += wgx * s;
-                        grd[q][1] += wgy * s;
-                        grd[q][2] += wgz * s;
-                    }
-                }
+        gather_all<0>(sv, sbz, vb, p.newtonian, Wx, Wy, Wz, Gx, Gy, Gz, val, grd);
         T u[3] = {P.u[0], P.u[1], P.u[2]};
         T dx[3];
         if (p.newtonian) {

@@ -509,3 +509,77 @@ def test_power_spectrum_of_random_particles_is_shot_noise():
     got = (pk[1:] * nm[1:]).sum()
     assert nm[1:].sum() == sel.sum()
     assert abs(got / expect - 1.0) < 0.06
+
+
+# ------------------------------------------------------- source assembly ----
+
+def test_sources_uniform_load_and_uniform_potentials():
+    """S00 = a Omega_m (uniform matter at rest), phi_prev = c, chi_prev = d: R = -3Hc c/dtau - 3Hc^2 d;
+    gradients vanish so F and Sig carry only the matter terms (zero here)."""
+    n, a, hc, dtp, dtp2, g4 = 8, 0.02, 0.3, 0.05, 0.04, 1.7
+    z = np.zeros((n, n, n)); c, d = 2e-5, 3e-7
+    s00 = np.full((n, n, n), a * OM)
+    R, F, S = O.sources(n, a, hc, dtp, dtp2, g4, OM, s00, np.zeros((3, n, n, n)), np.zeros((6, n, n, n)),
+                        np.full((n, n, n), c), np.full((n, n, n), d), np.full((n, n, n), c))
+    assert np.max(np.abs(R - (-3 * hc * c / dtp - 3 * hc * hc * d))) <= 1e-18
+    assert np.max(np.abs(F)) == 0.0 and np.max(np.abs(S)) <= 1e-30
+
+
+def test_sources_quadratic_terms_single_mode():
+    """phi = psi = A sin(2 pi x) (chi = 0): Q_ij = -2 d_i phi d_j phi, so Sig_xx = -2 TF(Q)_xx = 8/3 g^2,
+    Sig_yy = Sig_zz = -4/3 g^2, off-diagonals 0, with g the centred difference of phi (Eq. spacespace)."""
+    n, A = 16, 1e-3
+    x, y, zc = vertex_coords(n)
+    phi = A * np.sin(2 * np.pi * x)
+    g = A * np.cos(2 * np.pi * x) * math.sin(2 * np.pi / n) * n
+    zero = np.zeros((n, n, n))
+    R, F, S = O.sources(n, 0.1, 0.2, 0.05, 0.05, 1.0, OM, np.full((n, n, n), 0.1 * OM), np.zeros((3, n, n, n)),
+                        np.zeros((6, n, n, n)), phi, zero, phi)
+    assert np.max(np.abs(S[0] - 8.0 / 3.0 * g ** 2)) <= 1e-15
+    assert np.max(np.abs(S[3] + 4.0 / 3.0 * g ** 2)) <= 1e-15 and np.max(np.abs(S[5] + 4.0 / 3.0 * g ** 2)) <= 1e-15
+    assert np.max(np.abs(S[[1, 2, 4]])) <= 1e-18
+    # matter stress enters as 16 pi G a^-2 TF(S_ij): a pure xx stress of 3 units gives 2 units on xx
+    sij = np.zeros((6, n, n, n)); sij[0] = 3.0
+    _, _, S2 = O.sources(n, 0.5, 0.2, 0.05, 0.05, 1.25, OM, np.full((n, n, n), 0.5 * OM), np.zeros((3, n, n, n)), sij,
+                         zero, zero, zero)
+    assert np.allclose(S2[0], 4 * 1.25 / 0.25 * 2.0, rtol=1e-15) and np.allclose(S2[3], -4 * 1.25 / 0.25, rtol=1e-15)
+
+
+def test_sources_momentum_constraint_terms():
+    """F_i = 4piG a^-2 S0i - phi' d_i psi with phi' = (phi_{n-1} - phi_{n-2}) / dtau_{n-2} (Eq. momentumcontraint)."""
+    n, A, c, dtp2, a, g4 = 16, 1e-4, 3e-6, 0.02, 0.25, 0.9
+    x, y, zc = vertex_coords(n)
+    psi = A * np.sin(2 * np.pi * y)
+    g = A * np.cos(2 * np.pi * y) * math.sin(2 * np.pi / n) * n
+    zero = np.zeros((n, n, n))
+    s0i = np.zeros((3, n, n, n)); s0i[2] = 7.0
+    R, F, S = O.sources(n, a, 0.2, 0.05, dtp2, g4, OM, np.full((n, n, n), a * OM), s0i, np.zeros((6, n, n, n)),
+                        psi + c, zero, psi)
+    assert np.max(np.abs(F[0])) <= 1e-20
+    assert np.max(np.abs(F[1] + (c / dtp2) * g)) <= 1e-15 * np.max(np.abs(c / dtp2 * g)) + 1e-22
+    assert np.allclose(F[2], g4 / a ** 2 * 7.0, rtol=1e-15)
+
+
+def test_relativistic_growth_close_to_newtonian():
+    """Full relativistic step, one small plane wave: sub-horizon growth follows D(a) up to O(Hc^2/k^2) and
+    the discretisation loss of the Newtonian test (a few per cent for the n=1 mode of a 32 mesh)."""
+    from paper_2607_17929_gb300 import ics
+    n = 32
+    s = O.OracleSim(n, n ** 3, OM, BOX, 100.0, 0.0, 100)
+    a0 = s.a_n[0]
+    a_m = O.a_after(a0, -0.5 * s.dtau[0], OM, s.h0)
+    amp = 1e-4
+    pos, mom = ics.plane_wave_ics(n, amp, 1, a0, a_m, OM, BOX)
+    q = pos.copy()
+    q[:, 0] = (np.arange(n ** 3) % n + 0.5) / n
+    s.set_particles(pos, mom)
+    for _ in range(100):
+        s.step()
+    p1, _ = s.particles()
+    disp = (p1[:, 0] - q[:, 0] + 0.5) % 1.0 - 0.5
+    basis = np.sin(2 * np.pi * q[:, 0])
+    amp_end = -(disp @ basis) / (basis @ basis) * 2 * np.pi
+    d0, _ = ics.growth(a0, OM)
+    d1, _ = ics.growth(1.0, OM)
+    assert abs(amp_end / amp / (d1 / d0) - 1.0) <= 0.08
+    assert np.max(np.abs(s.field("chi"))) < 1e-2 * np.max(np.abs(s.field("phi")))

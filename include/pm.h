@@ -176,6 +176,28 @@ pm_status pm_get_tensor(pm_ctx *ctx, int which, double *dst);
  * stored sources.  Errors: INVALID_ARG, STATE, CUDA. */
 pm_status pm_power_spectrum(pm_ctx *ctx, int nbins, double *k, double *pk, int64_t *nmodes);
 
+/* pm_power_spectrum without any device allocation.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc where they
+ * want the diagnostic (code running under an allocator that forbids further
+ * allocation, or an application whose device memory is entirely handed to its
+ * own sub-allocator).  It needs no context.
+ * d_pos: n_part x 3 f64 positions in box units, DEVICE memory of the current
+ * device (host pointers are rejected with INVALID_ARG).  Computes the CIC
+ * mass-density contrast on an n_mesh^3 mesh (mass omega_m / n_part per
+ * particle) and the same binned P(k) as pm_power_spectrum into the HOST arrays
+ * k, pk, nmodes [nbins]; enqueued on `stream` (NULL = default) and synchronised.
+ * Limits: n_mesh of the form 2^a 3^b with a >= 3 and 8 <= n_mesh <= 64, and
+ * 2 <= nbins <= 512; larger sizes return PM_ERR_UNSUPPORTED_SIZE.
+ * Memory: all scratch (density, spectrum, bins, twiddle tables, about 4.3 MiB)
+ * is one file-scope __device__ array that every GPU loading the library holds
+ * until the process exits.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  Every call uses the same array, so calls that overlap on the GPU
+ * (on different streams or host threads) race and must be serialised by the
+ * caller.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA. */
+pm_status pm_power_spectrum_noalloc(const double *d_pos, int64_t n_part, int32_t n_mesh, double omega_m,
+                                    int32_t nbins, double *k, double *pk, int64_t *nmodes, void *stream);
+
 /* Step index (number of completed steps), a at that step, conformal time
  * since z_init.  Any pointer may be NULL. */
 pm_status pm_get_time(pm_ctx *ctx, int32_t *step, double *a, double *tau);

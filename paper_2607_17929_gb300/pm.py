@@ -63,6 +63,7 @@ def _load():
         "pm_get_schedule": ([vp, dp, dp, dp], C.c_int),
         "pm_get_timings": ([vp, dp, C.c_int, C.POINTER(i64)], C.c_int),
         "pm_put_particles": ([vp, vp, vp], C.c_int),
+        "pm_power_spectrum_noalloc": ([vp, i64, i32, C.c_double, i32, dp, dp, C.POINTER(i64), vp], C.c_int),
         "pm_save": ([vp, C.c_char_p], C.c_int),
         "pm_load": ([vp, C.c_char_p], C.c_int),
     }
@@ -77,7 +78,7 @@ lib = _load()
 
 EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_project", "pm_solve",
             "pm_update", "pm_step", "pm_put_particles", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
-            "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
+            "pm_power_spectrum_noalloc", "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
 
 
 def _ptr(a):
@@ -166,6 +167,20 @@ def pm_power_spectrum(ctx, nbins):
     _check(ctx, lib.pm_power_spectrum(ctx, nbins, k.ctypes.data_as(C.POINTER(C.c_double)),
                                       pk.ctypes.data_as(C.POINTER(C.c_double)),
                                       nm.ctypes.data_as(C.POINTER(C.c_int64))))
+    return k, pk, nm
+
+
+def pm_power_spectrum_noalloc(d_pos, n_mesh, omega_m, nbins, stream=None):
+    """P(k) of device positions without any device allocation (see include/pm.h for who needs it)."""
+    k = np.zeros(nbins); pk = np.zeros(nbins); nm = np.zeros(nbins, dtype=np.int64)
+    n_part = d_pos.shape[0] if hasattr(d_pos, "shape") else len(d_pos) // 3
+    st = lib.pm_power_spectrum_noalloc(_ptr(d_pos), int(n_part), int(n_mesh), float(omega_m), int(nbins),
+                                       k.ctypes.data_as(C.POINTER(C.c_double)),
+                                       pk.ctypes.data_as(C.POINTER(C.c_double)),
+                                       nm.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       getattr(stream, "cuda_stream", stream))
+    if st != PM_OK:
+        raise PMError(st, "pm_power_spectrum_noalloc failed")
     return k, pk, nm
 
 

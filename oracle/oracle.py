@@ -53,6 +53,8 @@ def lib():
         L.or_sources_flat.argtypes = [C.c_int] + [C.c_double] * 6 + [C.c_int, C.c_int] + [_dp] * 9
         L.or_kick_drift.argtypes = [C.c_int, _dp, _dp, C.c_long] + [C.c_double] * 4 + [C.c_int, _dp, _dp, _dp]
         L.or_polarisations.argtypes = [np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS"), _dp, _dp, _dp]
+        L.or_project_vertex.argtypes = [C.c_int, np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS"), _dp,
+                                        _dp, C.c_long, C.c_double, C.c_double, _dp, _dp, _dp]
         L.or_sim_create.restype = C.c_void_p
         L.or_sim_create.argtypes = [C.c_int, C.c_long, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
                                     C.c_int]
@@ -125,6 +127,17 @@ def project(n, pos, mom, mass, a, phi_prev, chi_prev, newtonian=False):
                      np.ascontiguousarray(phi_prev, dtype=np.float64).reshape(-1),
                      np.ascontiguousarray(chi_prev, dtype=np.float64).reshape(-1), int(newtonian), s00, s0i, sij)
     return s00.reshape(n, n, n), s0i.reshape(3, n, n, n), sij.reshape(6, n, n, n)
+
+
+def project_vertex(n, v, pos, mom, mass, a, phi_p=None, chi_p=None):
+    """Projection [S00, S0x, S0y, S0z, Sxx, Sxy, Sxz, Syy, Syz, Szz] at vertex v=(x, y, z) from the listed particles."""
+    pos = _flat(pos); mom = _flat(mom)
+    npart = pos.size // 3
+    phi_p = np.zeros(npart) if phi_p is None else _flat(phi_p)
+    chi_p = np.zeros(npart) if chi_p is None else _flat(chi_p)
+    out = np.zeros(10)
+    lib().or_project_vertex(n, np.asarray(v, dtype=np.int64), pos, mom, npart, mass, a, phi_p, chi_p, out)
+    return out
 
 
 def tensor_step(h, v, k2, hc, dt, s):

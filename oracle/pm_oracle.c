@@ -304,6 +304,37 @@ void or_project(int n, const double *pos, const double *mom, long np, double mas
     }
 }
 
+/* The same projection evaluated at one vertex v from a list of particles
+ * (those whose cells touch v), with phi_p, chi_p given per particle:
+ * out = [S00, S0x, S0y, S0z, Sxx, Sxy, Sxz, Syy, Syz, Szz] at v. */
+void or_project_vertex(int n, const long v[3], const double *pos, const double *mom, long np, double mass, double a,
+                       const double *phi_p, const double *chi_p, double *out)
+{
+    for (int c = 0; c < 10; c++) out[c] = 0.0;
+    double vol = (double)n * n * n;
+    for (long p = 0; p < np; p++) {
+        const double *x = pos + 3 * p, *u = mom + 3 * p;
+        long i[3];
+        double f[3], w = 1.0;
+        for (int d = 0; d < 3; d++) {
+            cic_axis(x[d], n, &i[d], &f[d]);
+            long off = wrap(v[d] - i[d], n);
+            if (off == 0) w *= 1.0 - f[d];
+            else if (off == 1) w *= f[d];
+            else w = 0.0;
+        }
+        if (w == 0.0) continue;
+        double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        double E = sqrt(a * a + u2);
+        double ph = phi_p[p], ch = chi_p[p];
+        out[0] += vol * w * mass * E * (1.0 + 3.0 * ph + ph * u2 / (E * E));
+        for (int d = 0; d < 3; d++) out[1 + d] += vol * w * mass * u[d] * (1.0 + 4.0 * ph - ch);
+        const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+        for (int c = 0; c < 6; c++)
+            out[4 + c] += vol * w * mass * u[ii[c]] * u[jj[c]] * (1.0 + 3.0 * ph - ph * u2 / (E * E)) / E;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Field equations.                                                          */
 /* ------------------------------------------------------------------------ */

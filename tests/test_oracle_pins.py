@@ -583,3 +583,17 @@ def test_relativistic_growth_close_to_newtonian():
     d1, _ = ics.growth(1.0, OM)
     assert abs(amp_end / amp / (d1 / d0) - 1.0) <= 0.08
     assert np.max(np.abs(s.field("chi"))) < 1e-2 * np.max(np.abs(s.field("phi")))
+
+
+def test_project_vertex_equals_full_projection():
+    """The one-vertex projection used by the full-size sampled checks agrees with the mesh projection."""
+    n = 8
+    rng = np.random.default_rng(13)
+    pos = rng.random((400, 3)); mom = rng.standard_normal((400, 3)) * 0.01; m = 0.31 / 400; a = 0.05
+    phi = 1e-4 * rng.standard_normal((n, n, n)); chi = 1e-6 * rng.standard_normal((n, n, n))
+    s00, s0i, sij = O.project(n, pos, mom, m, a, phi, chi)
+    php = O.cic_interp(phi, pos); chp = O.cic_interp(chi, pos)
+    for v in [(0, 0, 0), (7, 3, 5), (2, 7, 0)]:
+        out = O.project_vertex(n, v, pos, mom, m, a, php, chp)
+        ref = np.concatenate([[s00[v[2], v[1], v[0]]], s0i[:, v[2], v[1], v[0]], sij[:, v[2], v[1], v[0]]])
+        assert np.max(np.abs(out - ref)) <= 1e-13 * np.max(np.abs(ref))

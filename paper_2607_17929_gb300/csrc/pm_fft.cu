@@ -321,21 +321,50 @@ void col_pass(Ctx &c, int nf, const Ptrs &p, int64_t stride_j, int64_t ncols, in
 // ---------------------------------------------------------------------------
 // Compile-time-N passes (register-resident radix stages, see pm_fft_core.cuh).
 // ---------------------------------------------------------------------------
-template <class T, int N> struct Lines {
+// Shape of the FP32 column passes for power-of-two sizes >= 64 (ZP: the z pass,
+// whose points are a whole plane apart, else the y pass): points per thread,
+// lines per block (line width sets the contiguous row segment) and the threads
+// per SM the register budget must allow.  Chosen by timing at 512^3.
+#ifndef PM_COLY_P
+#define PM_COLY_P 8
+#endif
+#ifndef PM_COLY_L
+#define PM_COLY_L 8
+#endif
+#ifndef PM_COLY_TPSM
+#define PM_COLY_TPSM 1536
+#endif
+#ifndef PM_COLZ_P
+#define PM_COLZ_P 16
+#endif
+#ifndef PM_COLZ_L
+#define PM_COLZ_L 16
+#endif
+#ifndef PM_COLZ_TPSM
+#define PM_COLZ_TPSM 1024
+#endif
+
+template <class T, int N, bool ZP = false> struct Lines {
+    static constexpr bool tuned = sizeof(T) == 4 && N % 3 != 0 && N >= 64;
+    static constexpr int PP = ZP ? PM_COLZ_P : PM_COLY_P;
+    static constexpr int CP = tuned && PP != 8 ? PP : 0;  // 0: default points per thread
     static constexpr int TL = fftc::Geo<N>::TL;
-    // lines per block of the column passes: 64-byte row segments, at least 128 threads
-    static constexpr int col0 = sizeof(T) == 4 ? 8 : 4;
-    static constexpr int col1 = col0 * TL < 128 ? 128 / TL : col0;
-    static constexpr int col = col1 * TL > 512 ? 512 / TL : col1;
+    static constexpr int TLC = fftc::Geo<N, CP>::TL;
+    // lines per block of the column passes: 64-byte row segments by default, >= 128 threads
+    static constexpr int col0 = tuned ? (ZP ? PM_COLZ_L : PM_COLY_L) : (sizeof(T) == 4 ? 8 : 4);
+    static constexpr int col1 = col0 * TLC < 128 ? 128 / TLC : col0;
+    static constexpr int col = col1 * TLC > 1024 ? 1024 / TLC : col1;
     static constexpr int row = TL >= 256 ? 1 : 256 / TL;               // row pairs per block, x passes
-    // resident blocks per SM the register allocation must allow (P = 8 sizes)
-    static constexpr int col_min_blocks = fftc::Geo<N>::P == 8 ? (sizeof(T) == 4 ? 1536 / (TL * col) : 1024 / (TL * col)) : 1;
+    // resident blocks per SM the register allocation must allow
+    static constexpr int tpsm = tuned ? (ZP ? PM_COLZ_TPSM : PM_COLY_TPSM)
+                                      : (fftc::Geo<N>::P == 8 ? (sizeof(T) == 4 ? 1536 : 1024) : 0);
+    static constexpr int col_min_blocks = tpsm / (TLC * col) > 0 ? tpsm / (TLC * col) : 1;
 };
 
-template <class T, int N> size_t col_fast_smem()
+template <class T, int N, bool ZP> size_t col_fast_smem()
 {
     using G = fftc::Geo<N>;
-    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)N * Lines<T, N>::col);
+    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)N * Lines<T, N, ZP>::col);  // TWN does not depend on P
 }
 template <class T, int N> size_t row_fast_smem()
 {
@@ -343,14 +372,15 @@ template <class T, int N> size_t row_fast_smem()
     return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)Lines<T, N>::row * fftc::RowIdx<N>::pitch);
 }
 
-template <class T, int N, int DIR>
-__global__ void __launch_bounds__(fftc::Geo<N>::TL * Lines<T, N>::col, Lines<T, N>::col_min_blocks)
-k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t stride_j, int64_t ncols,
-           int64_t stride_b, int64_t nlines)
+template <class T, int N, int DIR, bool ZP>
+__global__ void __launch_bounds__(Lines<T, N, ZP>::TLC * Lines<T, N, ZP>::col, Lines<T, N, ZP>::col_min_blocks)
+k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t stride_j,
+           int64_t ncols, int64_t stride_b, int64_t nlines)
 {
     using C = typename Cplx<T>::type;
-    using G = fftc::Geo<N>;
-    constexpr int L = Lines<T, N>::col;
+    constexpr int CP = Lines<T, N, ZP>::CP;
+    using G = fftc::Geo<N, CP>;
+    constexpr int L = Lines<T, N, ZP>::col;
     extern __shared__ __align__(16) unsigned char smem[];
     C *tw = reinterpret_cast<C *>(smem);
     C *buf = tw + G::TWN;
@@ -363,12 +393,12 @@ k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__re
     C v[G::P];
 #pragma unroll
     for (int i = 0; i < G::P; i++)
-        v[i] = ok ? data[base + (int64_t)fftc::in_pos<N>(t, i) * stride_j] : fftc::mk<C>(0, 0);
+        v[i] = ok ? data[base + (int64_t)fftc::in_pos<N, CP>(t, i) * stride_j] : fftc::mk<C>(0, 0);
     __syncthreads();
-    fftc::fft<C, N, DIR>(v, t, buf, tw, fftc::ColIdx{L, l});
+    fftc::fft<C, N, DIR, CP>(v, t, buf, tw, fftc::ColIdx{L, l});
     if (ok) {
 #pragma unroll
-        for (int i = 0; i < G::P; i++) data[base + (int64_t)fftc::out_pos<N>(t, i) * stride_j] = v[i];
+        for (int i = 0; i < G::P; i++) data[base + (int64_t)fftc::out_pos<N, CP>(t, i) * stride_j] = v[i];
     }
 }
 
@@ -464,21 +494,32 @@ template <class T, int N> struct FastPasses {
         static bool done = false;
         if (done) return;
         done = true;
-        cudaFuncSetAttribute(k_col_fast<T, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_fast_smem<T, N>());
-        cudaFuncSetAttribute(k_col_fast<T, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_fast_smem<T, N>());
-        cudaFuncSetAttribute(k_r2c_fast<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fast_smem<T, N>());
-        cudaFuncSetAttribute(k_c2r_fast<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fast_smem<T, N>());
+        auto set = [](auto k, size_t b) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); };
+        set(k_col_fast<T, N, -1, false>, col_fast_smem<T, N, false>());
+        set(k_col_fast<T, N, 1, false>, col_fast_smem<T, N, false>());
+        set(k_col_fast<T, N, -1, true>, col_fast_smem<T, N, true>());
+        set(k_col_fast<T, N, 1, true>, col_fast_smem<T, N, true>());
+        set(k_r2c_fast<T, N>, row_fast_smem<T, N>());
+        set(k_c2r_fast<T, N>, row_fast_smem<T, N>());
     }
-    static void cols(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    template <bool ZP> static void cols_t(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
     {
-        constexpr int L = Lines<T, N>::col;
+        constexpr int L = Lines<T, N, ZP>::col;
+        constexpr int threads = Lines<T, N, ZP>::TLC * L;
         dim3 grid((unsigned)((nl + L - 1) / L), nf);
         const auto *tw = reinterpret_cast<const typename Cplx<T>::type *>(c.tw2);
+        const size_t sm = col_fast_smem<T, N, ZP>();
         if (dir < 0)
-            k_col_fast<T, N, -1><<<grid, fftc::Geo<N>::TL * L, col_fast_smem<T, N>(), c.stream>>>(p, tw, sj, nc, sb, nl);
+            k_col_fast<T, N, -1, ZP><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
         else
-            k_col_fast<T, N, 1><<<grid, fftc::Geo<N>::TL * L, col_fast_smem<T, N>(), c.stream>>>(p, tw, sj, nc, sb, nl);
+            k_col_fast<T, N, 1, ZP><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
         c.launches++;
+    }
+    // a z pass has no batch stride (its lines are the whole (ky, kx) plane)
+    static void cols(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    {
+        if (sb == 0) cols_t<true>(c, nf, p, sj, nc, sb, nl, dir);
+        else cols_t<false>(c, nf, p, sj, nc, sb, nl, dir);
     }
     static void rows(Ctx &c, int nf, const Ptrs &pi, const Ptrs &po, int dir)
     {

@@ -138,8 +138,9 @@ __host__ __device__ constexpr int tw_offset(int n, int s)
     return o;
 }
 
-template <int N> struct Geo {
-    static constexpr int P = (N % 3 == 0) ? 24 : 8;
+// PP = points per thread (0: 8, or 24 when N has a factor 3); every radix must divide it
+template <int N, int PP = 0> struct Geo {
+    static constexpr int P = PP ? PP : ((N % 3 == 0) ? 24 : 8);
     static constexpr int TL = N / P;
     static constexpr int NS = nstages(N);
     static constexpr int R0 = radix_at(N, 0);
@@ -149,21 +150,21 @@ template <int N> struct Geo {
 };
 
 // point index held in register i: input order of the first stage, output order of the last
-template <int N> __device__ __forceinline__ int in_pos(int t, int i)
+template <int N, int PP = 0> __device__ __forceinline__ int in_pos(int t, int i)
 {
-    constexpr int R = Geo<N>::R0;
-    return t + Geo<N>::TL * (i / R) + (i % R) * (N / R);
+    constexpr int R = Geo<N, PP>::R0;
+    return t + Geo<N, PP>::TL * (i / R) + (i % R) * (N / R);
 }
-template <int N> __device__ __forceinline__ int out_pos(int t, int i)
+template <int N, int PP = 0> __device__ __forceinline__ int out_pos(int t, int i)
 {
-    constexpr int R = Geo<N>::RL;
-    return t + Geo<N>::TL * (i / R) + (i % R) * (N / R);
+    constexpr int R = Geo<N, PP>::RL;
+    return t + Geo<N, PP>::TL * (i / R) + (i % R) * (N / R);
 }
 
-template <class C, int N, int S, int DIR>
-__device__ __forceinline__ void bfly(C (&v)[Geo<N>::P], int t, const C *__restrict__ tw)
+template <class C, int N, int PP, int S, int DIR>
+__device__ __forceinline__ void bfly(C (&v)[Geo<N, PP>::P], int t, const C *__restrict__ tw)
 {
-    constexpr int R = radix_at(N, S), Ns = span_before(N, S), P = Geo<N>::P, TL = Geo<N>::TL;
+    constexpr int R = radix_at(N, S), Ns = span_before(N, S), P = Geo<N, PP>::P, TL = Geo<N, PP>::TL;
 #pragma unroll
     for (int q = 0; q < P / R; q++) {
         if constexpr (S > 0) {
@@ -181,11 +182,11 @@ __device__ __forceinline__ void bfly(C (&v)[Geo<N>::P], int t, const C *__restri
 }
 
 // outputs of stage S -> shared memory -> inputs of stage S+1
-template <class C, int N, int S, class Idx>
-__device__ __forceinline__ void exchange(C (&v)[Geo<N>::P], int t, C *sm, Idx sidx)
+template <class C, int N, int PP, int S, class Idx>
+__device__ __forceinline__ void exchange(C (&v)[Geo<N, PP>::P], int t, C *sm, Idx sidx)
 {
     constexpr int R = radix_at(N, S), Ns = span_before(N, S), R2 = radix_at(N, S + 1);
-    constexpr int P = Geo<N>::P, TL = Geo<N>::TL;
+    constexpr int P = Geo<N, PP>::P, TL = Geo<N, PP>::TL;
 #pragma unroll
     for (int q = 0; q < P / R; q++) {
         const int b = t + TL * q;
@@ -203,22 +204,22 @@ __device__ __forceinline__ void exchange(C (&v)[Geo<N>::P], int t, C *sm, Idx si
     __syncthreads();
 }
 
-template <class C, int N, int S, int DIR, class Idx>
-__device__ __forceinline__ void run_from(C (&v)[Geo<N>::P], int t, C *sm, const C *tw, Idx sidx)
+template <class C, int N, int PP, int S, int DIR, class Idx>
+__device__ __forceinline__ void run_from(C (&v)[Geo<N, PP>::P], int t, C *sm, const C *tw, Idx sidx)
 {
-    bfly<C, N, S, DIR>(v, t, tw);
-    if constexpr (S + 1 < Geo<N>::NS) {
-        exchange<C, N, S>(v, t, sm, sidx);
-        run_from<C, N, S + 1, DIR>(v, t, sm, tw, sidx);
+    bfly<C, N, PP, S, DIR>(v, t, tw);
+    if constexpr (S + 1 < Geo<N, PP>::NS) {
+        exchange<C, N, PP, S>(v, t, sm, sidx);
+        run_from<C, N, PP, S + 1, DIR>(v, t, sm, tw, sidx);
     }
 }
 
 // In-register FFT of one line: v holds in_pos order on entry, out_pos order on exit.
 // Every thread of the block must call it (it synchronises the block).
-template <class C, int N, int DIR, class Idx>
-__device__ __forceinline__ void fft(C (&v)[Geo<N>::P], int t, C *sm, const C *tw, Idx sidx)
+template <class C, int N, int DIR, int PP = 0, class Idx>
+__device__ __forceinline__ void fft(C (&v)[Geo<N, PP>::P], int t, C *sm, const C *tw, Idx sidx)
 {
-    run_from<C, N, 0, DIR>(v, t, sm, tw, sidx);
+    run_from<C, N, PP, 0, DIR>(v, t, sm, tw, sidx);
 }
 
 // Shared-memory index maps.  Column kernels store [j][line] with the row

@@ -424,7 +424,7 @@ __device__ __forceinline__ void gather_all(const Vtx4<T> *sv, const T *sbz, int 
 // the tile go to shared memory once; each thread then gathers the CIC value
 // and centred-difference gradients for one particle from there.
 template <class T>
-__global__ void __launch_bounds__(KD_THREADS) k_kick_drift(const __grid_constant__ KdParams<T> p)
+__global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_drift(const __grid_constant__ KdParams<T> p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Vtx4<T> *sv = reinterpret_cast<Vtx4<T> *>(smem);              // [KNV]

@@ -217,3 +217,23 @@ def test_mixed_precision_ten_steps_32cubed(pm):
     assert worst["u"] < 1e-5 and rms_cells < 1e-6 and dx < 1e-4
     for k in ("chi", "B", "Fx", "Sxx", "h+", "hx"):
         assert worst[k] < 1e-3, (k, worst[k])
+
+
+@pytest.mark.parametrize("n,n_side,box,newtonian", [(64, 64, 640.0, False), (128, 48, 1280.0, True)])
+def test_mixed_precision_tuned_fft_sizes(pm, n, n_side, box, newtonian):
+    """Mixed form at sizes whose FP32 column passes use the tuned shapes (16 points per thread on
+    z lines), against the FP64 oracle with the bounds of the 32^3 mixed test."""
+    orc, g, pos, mom = make_pair(pm, n, n_side, box, 8, pm.PM_MIXED, newtonian=newtonian)
+    for _ in range(2):
+        orc.step()
+        g.step()
+    e = compare(orc, g, n, full=not newtonian)
+    p_g, _ = g.particles()
+    p_o, _ = orc.particles()
+    rms_cells = float(np.sqrt(np.mean(wrapdiff(p_g, p_o) ** 2)) * n)
+    g.close()
+    assert e["phi"] < 1e-5 and e["u"] < 1e-5 and rms_cells < 1e-6, (e, rms_cells)
+    if not newtonian:
+        assert e["R"] < 1e-5
+        for k in ("chi", "B", "Fx", "Sxx", "h+", "hx"):
+            assert e[k] < 1e-3, (k, e[k])

@@ -197,6 +197,98 @@ def half_step_back(a0, dtau0, box):
     return a
 
 
+ENSEMBLE_SIDES = (64,) * 16 + (128,) * 16 + (192,) * 16
+
+
+def ensemble_specs():
+    """48 boxes of uneven size: 16 each at 64^3, 128^3 and 192^3 mesh with one particle per cell; box b has
+    seed 1000 + b and a box length drawn uniformly from 200-1000 Mpc/h by a generator seeded with that seed."""
+    import numpy as np
+    return [(n, float(np.random.default_rng(1000 + b).uniform(200.0, 1000.0)), 1000 + b)
+            for b, n in enumerate(ENSEMBLE_SIDES)]
+
+
+def ensemble_bench(pm, torch, steps, warmup):
+    """boxes*steps/s of the batched ensemble (one captured graph per step, autotuned stream count) against
+    looping the single-box pm_step over the same boxes on one stream.  Inputs resident in HBM."""
+    specs = ensemble_specs()
+    inputs = []
+    t_ic = time.perf_counter()
+    for n, box, seed in specs:
+        probe = pm.PM(8, 8, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED)
+        a_n, dtau, _ = probe.schedule()
+        probe.close()
+        pos, mom = make_ics(n, box, seed, a_n[0], half_step_back(a_n[0], dtau[0], box))
+        inputs.append((torch.from_numpy(pos).cuda(), torch.from_numpy(mom).cuda()))
+    t_ic = time.perf_counter() - t_ic
+    nb = len(specs)
+
+    # looping the single-box path: one context per box, all on one stream, pm_step box after box
+    stream = torch.cuda.current_stream()
+    sims = []
+    for (n, box, _), (p, u) in zip(specs, inputs):
+        g = pm.PM(n, n ** 3, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED, 0, stream)
+        g.set_particles(p, u)
+        sims.append(g)
+    for _ in range(warmup):
+        for g in sims:
+            g.step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        for g in sims:
+            g.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = ev0.elapsed_time(ev1) / steps
+    for g in sims:
+        g.close()
+    del sims
+    torch.cuda.empty_cache()
+
+    # the ensemble: one graph per step on k streams
+    cfgs = [dict(n_mesh=n, n_part=n ** 3, box_mpch=box, omega_m=OM, z_init=ZI, n_steps=N_STEPS_SCHEDULE,
+                 precision=pm.PM_MIXED) for n, box, _ in specs]
+    e = pm.pm_ensemble_init(cfgs)
+    for b, (p, u) in enumerate(inputs):
+        pm.pm_ensemble_set_particles(e, b, p, u)
+    pm.pm_ensemble_step(e, use_graph=False)
+    k = pm.pm_ensemble_tune(e)
+    es = torch.cuda.ExternalStream(pm.pm_ensemble_stream(e))
+    for _ in range(warmup):
+        pm.pm_ensemble_step(e, use_graph=True)
+    pm.pm_ensemble_sync(e)
+    ev0.record(es)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pm.pm_ensemble_step(e, use_graph=True)
+    ev1.record(es)
+    pm.pm_ensemble_sync(e)
+    wall_ms = 1e3 * (time.perf_counter() - t0) / steps
+    ev1.synchronize()
+    ens_ms = ev0.elapsed_time(ev1) / steps
+    # the same streams without graphs, for reference
+    ev0.record(es)
+    for _ in range(steps):
+        pm.pm_ensemble_step(e, use_graph=False)
+    ev1.record(es)
+    pm.pm_ensemble_sync(e)
+    ev1.synchronize()
+    nog_ms = ev0.elapsed_time(ev1) / steps
+    pm.pm_ensemble_destroy(e)
+    del inputs
+    torch.cuda.empty_cache()
+    part = sum(n ** 3 for n, _, _ in specs)
+    return {"metric": "boxes*steps/s", "value": nb / (ens_ms * 1e-3), "ms_per_step": ens_ms,
+            "host_wall_ms_per_step": wall_ms, "loop_value": nb / (loop_ms * 1e-3), "loop_ms_per_step": loop_ms,
+            "speedup_over_loop": loop_ms / ens_ms, "streams": k, "no_graph_ms_per_step": nog_ms,
+            "particle_updates_per_s": part / (ens_ms * 1e-3), "steps": steps, "warmup": warmup,
+            "config": "48 boxes: 16 x 64^3, 16 x 128^3, 16 x 192^3 mesh, one particle per cell, box U(200,1000) "
+                      "Mpc/h, seeds 1000+b, mixed precision, same Zel'dovich/BBKS recipe at z=100",
+            "ic_seconds": round(t_ic, 1)}
+
+
 def cpu_oracle_rate(n, steps, box):
     """Particle updates per second of the FP64 C oracle (single thread) on an n^3 sample."""
     from oracle import oracle as O
@@ -256,6 +348,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -362,6 +456,10 @@ def main():
         del sim64
     torch.cuda.empty_cache()
 
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = ensemble_bench(pm, torch, args.ensemble_steps, 3)
+
     # roofline of the dominant kernel
     peak, peak_kind = load_peaks()
     dom = max(KERNELS, key=lambda k: kern.get(k, 0.0))
@@ -407,6 +505,7 @@ def main():
             "design_roofline_frac": design_bytes / (ms_max * 1e-3) / 1e9 / peak,
             "roofline": roofline,
             "fp64": fp64,
+            "ensemble": ensemble,
             "e2e": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                     "how": "pm_put_particles(pinned host f64 pos, mom) + pm_step + pm_get_particles(pinned host)"},

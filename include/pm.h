@@ -219,6 +219,47 @@ pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n, int64_t *launches);
 pm_status pm_save(pm_ctx *ctx, const char *path);
 pm_status pm_load(pm_ctx *ctx, const char *path);
 
+/* ------------------------------------------------------------------------
+ * Batched ensemble of independent boxes (each its own n_mesh, n_part,
+ * box_mpch and seed; all with the same n_steps, stepped in lockstep).  The
+ * paper runs one box per job; stepping many boxes together keeps the GPU
+ * busy when single boxes are small.  Each box is a full pm_ctx; an ensemble
+ * step issues every box's pm_step on one of K streams and, with use_graph,
+ * captures the whole step into one CUDA graph launched on the ensemble's own
+ * stream.  The ensemble owns its streams (cfg.stream is ignored).
+ * ------------------------------------------------------------------------ */
+typedef struct pm_ensemble pm_ensemble;
+
+/* Create nbox contexts from cfgs[nbox].  Errors: INVALID_ARG (n_steps differ),
+ * UNSUPPORTED_SIZE, OOM, CUDA (the partially built ensemble is released). */
+pm_status pm_ensemble_init(const pm_config *cfgs, int32_t nbox, pm_ensemble **out);
+void pm_ensemble_destroy(pm_ensemble *e);
+const char *pm_ensemble_last_error(const pm_ensemble *e);
+
+/* The context of box `box`, for the single-box getters (pm_get_particles,
+ * pm_get_field, pm_power_spectrum, ...).  Do not destroy it. */
+pm_status pm_ensemble_box(pm_ensemble *e, int32_t box, pm_ctx **ctx);
+
+/* pm_set_particles for one box; synchronises. */
+pm_status pm_ensemble_set_particles(pm_ensemble *e, int32_t box, const double *pos, const double *mom);
+
+/* One step of every box.  use_graph != 0 captures the step into a CUDA graph
+ * (one launch); the first step after pm_ensemble_init or set_particles should
+ * run with use_graph = 0 so that kernel attributes are set outside capture.
+ * Asynchronous on the ensemble stream; pm_ensemble_sync waits for it. */
+pm_status pm_ensemble_step(pm_ensemble *e, int32_t use_graph);
+pm_status pm_ensemble_sync(pm_ensemble *e);
+
+/* The ensemble's own stream (a cudaStream_t), on which every ensemble step is
+ * launched and completes; callers may record events on it or make their
+ * streams wait on it.  Owned by the ensemble. */
+pm_status pm_ensemble_stream(pm_ensemble *e, void **stream);
+
+/* Autotuner: times one graph-captured ensemble step for each candidate number
+ * of streams (1, 2, 4, ... up to nbox, at most 32) and keeps the fastest;
+ * *n_streams receives it.  Each trial advances every box by one step. */
+pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams);
+
 #ifdef __cplusplus
 }
 #endif

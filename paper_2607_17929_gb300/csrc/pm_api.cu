@@ -7,9 +7,6 @@
 
 #include "pm_internal.cuh"
 
-struct pm_ctx {
-    pm::Ctx c;
-};
 
 namespace pm {
 
@@ -739,7 +736,7 @@ pm_status pm_update(pm_ctx *ctx)
     c.mark(EV_END);
     c.timing_on = false;
     if (st) return st;
-    c.window = std::min<int64_t>(c.window + 1, Ctx::RING);
+    if (!c.no_timing) c.window = std::min<int64_t>(c.window + 1, Ctx::RING);
     rotate(c);
     c.step += 1;
     c.stage = 0;

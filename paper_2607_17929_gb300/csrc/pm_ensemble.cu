@@ -1,0 +1,220 @@
+// Batched ensemble: many independent boxes (each its own size, box length and
+// seed) stepped together.  Every box is a full single-box context; one
+// ensemble step issues all boxes' steps on K streams and captures them into
+// one CUDA graph, so the small boxes' kernels run concurrently and the CPU
+// issues one graph launch per step.  K is chosen by pm_ensemble_tune, which
+// times ensemble steps for a few candidate stream counts.  The step is
+// captured afresh each time (the potential ring, the particle ping-pong and
+// the step's scalars change from step to step) but the topology does not, so
+// the executable graph of the previous step is updated in place rather than
+// instantiated again.
+#include <chrono>
+#include <vector>
+
+#include "pm_internal.cuh"
+
+
+struct pm_ensemble {
+    std::vector<pm_ctx *> box;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraphExec_t exec = nullptr;  // executable graph of the last captured step
+    int exec_k = 0;                  // stream count it was captured with
+    int k = 1;                       // streams in use
+    std::string err;
+};
+
+namespace {
+
+constexpr int ENS_MAX_STREAMS = 32;
+
+pm_status ens_fail(pm_ensemble *e, pm_status st, const char *msg)
+{
+    e->err = msg;
+    return st;
+}
+
+// one ensemble step: fork from the origin stream to k streams, step every box
+// on stream (box % k), join back; with capture, the whole step becomes the graph
+// e->exec (updated in place when the previous one has the same topology)
+pm_status ens_issue(pm_ensemble *e, bool capture)
+{
+    cudaGraph_t graph = nullptr;
+    if (capture && cudaStreamBeginCapture(e->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return ens_fail(e, PM_ERR_CUDA, "cudaStreamBeginCapture failed");
+    cudaEventRecord(e->fork, e->origin);
+    for (int s = 0; s < e->k; s++) cudaStreamWaitEvent(e->streams[s], e->fork, 0);
+    pm_status st = PM_OK;
+    for (size_t b = 0; b < e->box.size() && st == PM_OK; b++) {
+        pm::Ctx &c = e->box[b]->c;
+        c.stream = e->streams[b % e->k];
+        c.no_timing = capture;
+        st = pm_step(e->box[b]);
+        c.no_timing = false;
+    }
+    for (int s = 0; s < e->k; s++) {
+        cudaEventRecord(e->joins[s], e->streams[s]);
+        cudaStreamWaitEvent(e->origin, e->joins[s], 0);
+    }
+    if (!capture) return st;
+    cudaError_t ce = cudaStreamEndCapture(e->origin, &graph);
+    if (st != PM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess || !graph) return ens_fail(e, PM_ERR_CUDA, "cudaStreamEndCapture failed");
+    bool updated = false;
+    if (e->exec && e->exec_k == e->k) {
+        cudaGraphExecUpdateResultInfo info{};
+        updated = cudaGraphExecUpdate(e->exec, graph, &info) == cudaSuccess;
+        if (!updated) cudaGetLastError();
+    }
+    if (!updated) {
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+        ce = cudaGraphInstantiate(&e->exec, graph, 0);
+        if (ce != cudaSuccess) {
+            e->exec = nullptr;
+            cudaGraphDestroy(graph);
+            return ens_fail(e, PM_ERR_CUDA, "cudaGraphInstantiate failed");
+        }
+        e->exec_k = e->k;
+    }
+    cudaGraphDestroy(graph);
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_ensemble_init(const pm_config *cfgs, int32_t nbox, pm_ensemble **out)
+{
+    if (!cfgs || !out || nbox < 1) return PM_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int b = 0; b < nbox; b++)
+        if (cfgs[b].n_steps != cfgs[0].n_steps) return PM_ERR_INVALID_ARG;  // boxes step in lockstep
+    pm_ensemble *e = new (std::nothrow) pm_ensemble();
+    if (!e) return PM_ERR_OOM;
+    e->streams.resize(ENS_MAX_STREAMS);
+    e->joins.resize(ENS_MAX_STREAMS);
+    bool ok = cudaStreamCreateWithFlags(&e->origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreate(&e->t0) == cudaSuccess && cudaEventCreate(&e->t1) == cudaSuccess;
+    for (int s = 0; s < ENS_MAX_STREAMS && ok; s++)
+        ok = cudaStreamCreateWithFlags(&e->streams[s], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e->joins[s], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        pm_ensemble_destroy(e);
+        return PM_ERR_CUDA;
+    }
+    e->k = nbox < 8 ? nbox : 8;
+    for (int b = 0; b < nbox; b++) {
+        pm_config cfg = cfgs[b];
+        cfg.stream = e->streams[b % e->k];
+        pm_ctx *c = nullptr;
+        pm_status st = pm_init(&cfg, &c);
+        if (st != PM_OK) {
+            pm_ensemble_destroy(e);
+            return st;
+        }
+        e->box.push_back(c);
+    }
+    *out = e;
+    return PM_OK;
+}
+
+void pm_ensemble_destroy(pm_ensemble *e)
+{
+    if (!e) return;
+    if (e->origin) cudaStreamSynchronize(e->origin);
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    for (pm_ctx *c : e->box) pm_destroy(c);
+    for (size_t s = 0; s < e->streams.size(); s++) {
+        if (e->streams[s]) cudaStreamDestroy(e->streams[s]);
+        if (e->joins[s]) cudaEventDestroy(e->joins[s]);
+    }
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->t0) cudaEventDestroy(e->t0);
+    if (e->t1) cudaEventDestroy(e->t1);
+    if (e->origin) cudaStreamDestroy(e->origin);
+    cudaGetLastError();
+    delete e;
+}
+
+const char *pm_ensemble_last_error(const pm_ensemble *e)
+{
+    return e ? e->err.c_str() : "null ensemble";
+}
+
+pm_status pm_ensemble_box(pm_ensemble *e, int32_t box, pm_ctx **ctx)
+{
+    if (!e || !ctx || box < 0 || box >= (int32_t)e->box.size()) return PM_ERR_INVALID_ARG;
+    *ctx = e->box[box];
+    return PM_OK;
+}
+
+pm_status pm_ensemble_set_particles(pm_ensemble *e, int32_t box, const double *pos, const double *mom)
+{
+    if (!e || box < 0 || box >= (int32_t)e->box.size()) return PM_ERR_INVALID_ARG;
+    pm_ctx *c = e->box[box];
+    c->c.stream = e->streams[box % e->k];
+    pm_status st = pm_set_particles(c, pos, mom);
+    if (st == PM_OK && cudaStreamSynchronize(c->c.stream) != cudaSuccess) return PM_ERR_CUDA;
+    return st;
+}
+
+pm_status pm_ensemble_step(pm_ensemble *e, int32_t use_graph)
+{
+    if (!e) return PM_ERR_INVALID_ARG;
+    if (!use_graph) return ens_issue(e, false);
+    pm_status st = ens_issue(e, true);
+    if (st != PM_OK) return st;
+    cudaError_t ce = cudaGraphLaunch(e->exec, e->origin);
+    return ce == cudaSuccess ? PM_OK : ens_fail(e, PM_ERR_CUDA, "cudaGraphLaunch failed");
+}
+
+pm_status pm_ensemble_sync(pm_ensemble *e)
+{
+    if (!e) return PM_ERR_INVALID_ARG;
+    return cudaStreamSynchronize(e->origin) == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+}
+
+pm_status pm_ensemble_stream(pm_ensemble *e, void **stream)
+{
+    if (!e || !stream) return PM_ERR_INVALID_ARG;
+    *stream = e->origin;
+    return PM_OK;
+}
+
+pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams)
+{
+    if (!e) return PM_ERR_INVALID_ARG;
+    const int cand[] = {1, 2, 4, 8, 16, 32};
+    float best = 1e30f;
+    int best_k = e->k;
+    for (int k : cand) {
+        if (k > (int)e->box.size() || k > ENS_MAX_STREAMS) break;
+        // a trial step per candidate (the boxes advance: tuning consumes schedule steps)
+        e->k = k;
+        if (cudaEventRecord(e->t0, e->origin) != cudaSuccess) return PM_ERR_CUDA;
+        pm_status st = pm_ensemble_step(e, 1);
+        if (st != PM_OK) return st;
+        cudaEventRecord(e->t1, e->origin);
+        if (cudaEventSynchronize(e->t1) != cudaSuccess) return PM_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e->t0, e->t1);
+        if (ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    e->k = best_k;
+    if (n_streams) *n_streams = best_k;
+    return PM_OK;
+}
+
+}  // extern "C"

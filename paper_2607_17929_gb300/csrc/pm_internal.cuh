@@ -124,9 +124,11 @@ struct Ctx {
     int64_t window = 0;       // completed steps in the current timing window
     int64_t launches = 0, launches_mark = 0;
 
+    bool no_timing = false;   // set while a step is captured into a CUDA graph (ensemble)
+
     void mark(int point)
     {
-        if (timing_on) cudaEventRecord(evr[stepc % RING][point], stream);
+        if (timing_on && !no_timing) cudaEventRecord(evr[stepc % RING][point], stream);
     }
 };
 
@@ -174,3 +176,8 @@ bool fast_fft_supported(int n);
 void fast_twiddles(int n, std::vector<double> &re_im);
 
 }  // namespace pm
+
+// the opaque context of the C ABI
+struct pm_ctx {
+    pm::Ctx c;
+};

@@ -63,6 +63,15 @@ def _load():
         "pm_get_schedule": ([vp, dp, dp, dp], C.c_int),
         "pm_get_timings": ([vp, dp, C.c_int, C.POINTER(i64)], C.c_int),
         "pm_put_particles": ([vp, vp, vp], C.c_int),
+        "pm_ensemble_init": ([C.c_void_p, i32, C.POINTER(vp)], C.c_int),
+        "pm_ensemble_destroy": ([vp], None),
+        "pm_ensemble_last_error": ([vp], C.c_char_p),
+        "pm_ensemble_box": ([vp, i32, C.POINTER(vp)], C.c_int),
+        "pm_ensemble_set_particles": ([vp, i32, vp, vp], C.c_int),
+        "pm_ensemble_step": ([vp, i32], C.c_int),
+        "pm_ensemble_sync": ([vp], C.c_int),
+        "pm_ensemble_tune": ([vp, C.POINTER(i32)], C.c_int),
+        "pm_ensemble_stream": ([vp, C.POINTER(vp)], C.c_int),
         "pm_power_spectrum_noalloc": ([vp, i64, i32, C.c_double, i32, dp, dp, C.POINTER(i64), vp], C.c_int),
         "pm_save": ([vp, C.c_char_p], C.c_int),
         "pm_load": ([vp, C.c_char_p], C.c_int),
@@ -78,7 +87,10 @@ lib = _load()
 
 EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_project", "pm_solve",
             "pm_update", "pm_step", "pm_put_particles", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
-            "pm_power_spectrum_noalloc", "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
+            "pm_power_spectrum_noalloc", "pm_ensemble_init", "pm_ensemble_destroy", "pm_ensemble_last_error",
+            "pm_ensemble_box", "pm_ensemble_set_particles", "pm_ensemble_step", "pm_ensemble_sync", "pm_ensemble_tune",
+            "pm_ensemble_stream",
+            "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
 
 
 def _ptr(a):
@@ -211,6 +223,65 @@ def pm_save(ctx, path):
 
 def pm_load(ctx, path):
     _check(ctx, lib.pm_load(ctx, os.fsencode(path)))
+
+
+def _echeck(e, st):
+    if st != PM_OK:
+        raise PMError(st, lib.pm_ensemble_last_error(e).decode() if e else "")
+
+
+def pm_ensemble_init(configs):
+    """configs: list of dicts with the PM() keyword arguments (n_mesh, n_part, box_mpch, omega_m, z_init,
+    z_final, n_steps, precision, flags)."""
+    arr = (pm_config * len(configs))()
+    for i, c in enumerate(configs):
+        arr[i] = pm_config(int(c["n_mesh"]), int(c.get("n_steps", 100)), int(c["n_part"]), float(c["box_mpch"]),
+                           float(c["omega_m"]), float(c["z_init"]), float(c.get("z_final", 0.0)),
+                           int(c.get("precision", PM_FP64)), int(c.get("flags", 0)), None)
+    h = C.c_void_p()
+    st = lib.pm_ensemble_init(C.cast(arr, C.c_void_p), len(configs), C.byref(h))
+    if st != PM_OK:
+        raise PMError(st, "pm_ensemble_init failed")
+    return h.value
+
+
+def pm_ensemble_destroy(e):
+    lib.pm_ensemble_destroy(e)
+
+
+def pm_ensemble_last_error(e):
+    return lib.pm_ensemble_last_error(e).decode()
+
+
+def pm_ensemble_box(e, box):
+    h = C.c_void_p()
+    _echeck(e, lib.pm_ensemble_box(e, int(box), C.byref(h)))
+    return h.value
+
+
+def pm_ensemble_set_particles(e, box, pos, mom):
+    _echeck(e, lib.pm_ensemble_set_particles(e, int(box), _ptr(pos), _ptr(mom)))
+
+
+def pm_ensemble_step(e, use_graph=True):
+    _echeck(e, lib.pm_ensemble_step(e, int(bool(use_graph))))
+
+
+def pm_ensemble_sync(e):
+    _echeck(e, lib.pm_ensemble_sync(e))
+
+
+def pm_ensemble_stream(e):
+    """The ensemble's stream handle (an int usable as torch.cuda.ExternalStream(handle))."""
+    h = C.c_void_p()
+    _echeck(e, lib.pm_ensemble_stream(e, C.byref(h)))
+    return h.value or 0
+
+
+def pm_ensemble_tune(e):
+    k = C.c_int32()
+    _echeck(e, lib.pm_ensemble_tune(e, C.byref(k)))
+    return k.value
 
 
 class PM:

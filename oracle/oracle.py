@@ -49,8 +49,11 @@ def lib():
                                  _dp, _dp, _dp]
         L.or_tensor_step_ri.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_power_spectrum.argtypes = [C.c_int, _dp, C.c_double, C.c_int, _dp, _dp, _i64p]
-        L.or_solve_sources_flat.argtypes = [C.c_int] + [C.c_double] * 8 + [C.c_int, C.c_int] + [_dp] * 7
-        L.or_sources_flat.argtypes = [C.c_int] + [C.c_double] * 6 + [C.c_int, C.c_int] + [_dp] * 9
+        L.or_solve_sources_flat.argtypes = ([C.c_int] + [C.c_double] * 8 + [C.c_int, C.c_int] + [_dp] * 7 +
+                                            [C.c_int, C.c_int, C.c_double, _dp])
+        L.or_sources_flat.argtypes = [C.c_int] + [C.c_double] * 6 + [C.c_int, C.c_int] + [_dp] * 9 + [C.c_int]
+        L.or_laplacian7.argtypes = [_dp, C.c_int, _dp]
+        L.or_hc_remainder.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
         L.or_kick_drift.argtypes = [C.c_int, _dp, _dp, C.c_long] + [C.c_double] * 4 + [C.c_int, _dp, _dp, _dp]
         L.or_polarisations.argtypes = [np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS"), _dp, _dp, _dp]
         L.or_project_vertex.argtypes = [C.c_int, np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS"), _dp,
@@ -159,29 +162,49 @@ def _flat(a):
 
 
 def sources(n, a, hc, dtau_prev, dtau_prev2, four_pi_g, omega_m, s00, s0i, sij, phi_prev, chi_prev, phi_prev2,
-            newtonian=False, bootstrap=False):
+            newtonian=False, bootstrap=False, full_hc=False):
     """Configuration-space sources R, F (3), Sig (6: xx,xy,xz,yy,yz,zz)."""
     nc = n ** 3
     R = np.zeros(nc); F = np.zeros(3 * nc); S = np.zeros(6 * nc)
     lib().or_sources_flat(n, a, hc, dtau_prev, dtau_prev2, four_pi_g, omega_m, int(newtonian), int(bootstrap),
                           _flat(s00), _flat(s0i), _flat(sij), _flat(phi_prev), _flat(chi_prev), _flat(phi_prev2),
-                          R, F, S)
+                          R, F, S, int(full_hc))
     return R.reshape(n, n, n), F.reshape(3, n, n, n), S.reshape(6, n, n, n)
 
 
 def solve_sources(n, R, F=None, Sig=None, *, a=1.0, hc=0.0, dtau_prev=1.0, dtau_prev2=1.0, dtau=1.0, hc_half=0.0,
-                  four_pi_g=1.0, omega_m=1.0, newtonian=False, bootstrap=False, tensor=None):
-    """Run the oracle's Fourier solve on given sources; returns phi, chi, B, tensor state."""
+                  four_pi_g=1.0, omega_m=1.0, newtonian=False, bootstrap=False, tensor=None, b_space=False,
+                  b_seed=False, b_decay=1.0, bstate=None):
+    """Run the oracle's Fourier solve on given sources; returns phi, chi, B, tensor state.  With b_space, B
+    comes from Eq. spacespace and `bstate` (complex (3, n, n, n), updated in place) carries B_k."""
     nc = n ** 3
     F = np.zeros(3 * nc) if F is None else _flat(F)
     Sig = np.zeros(6 * nc) if Sig is None else _flat(Sig)
     phi = np.zeros(nc); chi = np.zeros(nc); B = np.zeros(3 * nc)
     ts = np.zeros(8 * nc) if tensor is None else np.ascontiguousarray(tensor, dtype=np.complex128).view(
         np.float64).reshape(-1).copy()
+    bs = np.zeros(6 * nc) if bstate is None else bstate.view(np.float64).reshape(-1)
+    assert bstate is None or (bstate.dtype == np.complex128 and bstate.flags.c_contiguous and bstate.size == 3 * nc)
     lib().or_solve_sources_flat(n, a, hc, dtau_prev, dtau_prev2, dtau, hc_half, four_pi_g, omega_m, int(newtonian),
-                                int(bootstrap), _flat(R), F, Sig, phi, chi, B, ts)
+                                int(bootstrap), _flat(R), F, Sig, phi, chi, B, ts, int(b_space), int(b_seed),
+                                float(b_decay), bs)
     return (phi.reshape(n, n, n), chi.reshape(n, n, n), B.reshape(3, n, n, n),
             ts.view(np.complex128).reshape(4, n, n, n))
+
+
+def laplacian7(field):
+    n = field.shape[0]
+    out = np.zeros(n ** 3)
+    lib().or_laplacian7(_flat(field), n, out)
+    return out.reshape(field.shape)
+
+
+def hc_remainder(hc, dtau_prev2, phi, chi, phi_prev2):
+    """Nonlinear remainder Nl of Eq. fullHc on phi_{n-1}, chi_{n-1}, phi_{n-2}."""
+    n = phi.shape[0]
+    out = np.zeros(n ** 3)
+    lib().or_hc_remainder(n, hc, dtau_prev2, _flat(phi), _flat(chi), _flat(phi_prev2), out)
+    return out.reshape(phi.shape)
 
 
 def kick_drift(n, pos, mom, a_kick, a_drift, dtau_kick, dtau_drift, phi, chi, B, newtonian=False):
@@ -206,13 +229,15 @@ TENSOR_IDS = {"h+": 0, "hx": 1, "h+'": 2, "hx'": 3}
 class OracleSim:
     """The oracle's time stepper: set_particles() bootstraps, step() runs one PM step."""
 
-    def __init__(self, n_mesh, n_part, omega_m, box_mpch, z_init, z_final=0.0, n_steps=100, newtonian=False):
+    def __init__(self, n_mesh, n_part, omega_m, box_mpch, z_init, z_final=0.0, n_steps=100, newtonian=False,
+                 full_hc=False, b_space=False):
         self.n = int(n_mesh)
         self.np = int(n_part)
         self.omega_m = omega_m
         self.h0 = box_mpch / 2997.92458
         self.mass = omega_m / n_part
-        self._h = lib().or_sim_create(self.n, self.np, omega_m, box_mpch, z_init, z_final, n_steps, int(newtonian))
+        flags = int(bool(newtonian)) | (2 if full_hc else 0) | (4 if b_space else 0)
+        self._h = lib().or_sim_create(self.n, self.np, omega_m, box_mpch, z_init, z_final, n_steps, flags)
         self.n_steps = n_steps
         self.a_n, self.dtau, self.a_half = np.zeros(n_steps + 1), np.zeros(n_steps), np.zeros(n_steps)
         lib().or_sim_schedule(self._h, self.a_n, self.dtau, self.a_half)

@@ -22,6 +22,15 @@
  *  - quadratic terms in phi, psi are taken from the previous step, with no
  *    predictor-corrector iterations (Sec. 3.1);
  *  - Nyquist modes (any |n_i| = N/2) are removed from chi, B and h.
+ *  Two variants of the solve, each off by default:
+ *  - full Hamiltonian constraint (Eq. fullHc): the terms of Eq. fullHc that
+ *    are not linear in phi, psi move into the source of the linear solve,
+ *    evaluated once on the previous step's phi, psi and phi' (the paper's
+ *    predictor with no corrector iterations, Sec. 3.1);
+ *  - B_i from the trace-free space-space equation (Eq. spacespace): its
+ *    spin-1 part (d_tau + 2 Hc) B_j = W_j, integrated as d(a^2 B)/dtau = a^2 W
+ *    with W at the new time (backward Euler); the first step takes B from
+ *    the momentum constraint to start the integration.
  */
 #include <complex.h>
 #include <math.h>
@@ -349,7 +358,55 @@ typedef struct {
     double omega_m;
     int newtonian;
     int bootstrap;         /* quasi-static phi only (first solve) */
+    int full_hc;           /* nonlinear remainder of Eq. fullHc in the phi source */
+    int b_space;           /* B_i from Eq. spacespace (integrated) instead of the momentum constraint */
+    int b_seed;            /* with b_space: take this step's B from the momentum constraint */
+    double b_decay;        /* with b_space: (a_{n-1} / a_n)^2 */
 } or_solve_params;
+
+/* 7-point Laplacian (sum of the six neighbours - 6 f) / dx^2. */
+void or_laplacian7(const double *f, int n, double *out)
+{
+    long N = n;
+    for (long z = 0; z < N; z++)
+        for (long y = 0; y < N; y++)
+            for (long x = 0; x < N; x++) {
+                double s = f[idx3(x + 1, y, z, N)] + f[idx3(x - 1, y, z, N)] + f[idx3(x, y + 1, z, N)] +
+                           f[idx3(x, y - 1, z, N)] + f[idx3(x, y, z + 1, N)] + f[idx3(x, y, z - 1, N)];
+                out[(z * N + y) * N + x] = (s - 6.0 * f[(z * N + y) * N + x]) * (double)N * (double)N;
+            }
+}
+
+/*
+ * Nonlinear remainder of the Hamiltonian constraint, Eq. fullHc.  With the
+ * background (3/2) Hc^2 = 4piG a^2 rho_bar removed, Eq. fullHc reads
+ *   lin + Nl = 4piG a^-2 (S00 - a Omega_m),  lin = Lap phi - 3 Hc phi' - 3 Hc^2 psi,
+ *   Nl = (e^{2phi} - 1) Lap phi - 1/2 e^{2phi} |grad phi|^2
+ *        + 3/2 [(Hc - phi')^2 e^{-2psi} - Hc^2 + 2 Hc phi' + 2 Hc^2 psi].
+ * The bracket is regrouped exactly as Hc^2 (e^x - 1 - x) - 2 Hc phi' (e^x - 1)
+ * + phi'^2 e^x with x = -2 psi, so that nothing of size Hc^2 cancels.
+ * Evaluated on phi = phi_{n-1}, psi = phi_{n-1} - chi_{n-1} and
+ * phi' = (phi_{n-1} - phi_{n-2}) / dtau_prev2; Lap is the 7-point Laplacian
+ * and grad the centred difference.
+ */
+void or_hc_remainder(int n, double hc, double dtau_prev2, const double *phi, const double *chi,
+                     const double *phi_prev2, double *out)
+{
+    size_t nc = (size_t)n * n * n;
+    double *lap = malloc(sizeof(double) * nc), *g = malloc(sizeof(double) * 3 * nc);
+    or_laplacian7(phi, n, lap);
+    for (int d = 0; d < 3; d++) or_gradient(phi, n, d, g + d * nc);
+    for (size_t c = 0; c < nc; c++) {
+        double psi = phi[c] - chi[c];
+        double dphi = (phi[c] - phi_prev2[c]) / dtau_prev2;
+        double g2 = g[c] * g[c] + g[nc + c] * g[nc + c] + g[2 * nc + c] * g[2 * nc + c];
+        double x = -2.0 * psi;
+        out[c] = expm1(2.0 * phi[c]) * lap[c] - 0.5 * exp(2.0 * phi[c]) * g2 +
+                 1.5 * (hc * hc * (expm1(x) - x) - 2.0 * hc * dphi * expm1(x) + dphi * dphi * exp(x));
+    }
+    free(lap);
+    free(g);
+}
 
 /* ktilde_i = 2N sin(pi n_i / N): with it sum_i ktilde_i^2 is the eigenvalue of
  * minus the 7-point Laplacian. */
@@ -406,7 +463,7 @@ void or_tensor_step_ri(double *h, double *v, double k2, double hc, double dt, do
  *  Sig_ij = 16piG a^-2 (Sij - delta_ij S_kk/3) - 2 TF[2 d_i phi d_j phi
  *          - (d_i phi + d_i psi)(d_j phi + d_j psi)]   (Eq. spacespace),
  * with phi, psi, phi' from the previous step(s).  Bootstrap: R only, with
- * the (3 Hc/dtau) term dropped.
+ * the (3 Hc/dtau) term dropped.  full_hc: R -= Nl (or_hc_remainder).
  */
 void or_sources(int n, const or_solve_params *sp, const double *s00, const double *s0i, const double *sij,
                 const double *phi_prev, const double *chi_prev, const double *phi_prev2,
@@ -424,6 +481,12 @@ void or_sources(int n, const or_solve_params *sp, const double *s00, const doubl
                    - 3.0 * hc * hc * chi_prev[c];
     }
     if (sp->newtonian || sp->bootstrap) return;
+    if (sp->full_hc) {
+        double *nl = malloc(sizeof(double) * nc);
+        or_hc_remainder(n, hc, sp->dtau_prev2, phi_prev, chi_prev, phi_prev2, nl);
+        for (size_t c = 0; c < nc; c++) R[c] -= nl[c];
+        free(nl);
+    }
     double *psi = malloc(sizeof(double) * nc);
     double *gphi = malloc(sizeof(double) * 3 * nc), *gpsi = malloc(sizeof(double) * 3 * nc);
     for (size_t c = 0; c < nc; c++) psi[c] = phi_prev[c] - chi_prev[c];
@@ -464,11 +527,16 @@ void or_sources(int n, const or_solve_params *sp, const double *s00, const doubl
  *  B_i,k = 4 (delta_ij - kt_i kt_j / kt^2) F_j,k / kt^2     (spin-1 part of Eq. momentumcontraint)
  *  h_A:   s_A = e^A_ij Sig_ij,k, one Crank-Nicolson step    (spin-2 part of Eq. spacespace)
  * chi_0 = B_0 = h_0 = 0, and chi, B, h vanish on Nyquist modes.
+ * b_space (B from Eq. spacespace): with d_i -> i kt_i, the vector part of
+ * Sig is i (kt_i V_j + kt_j V_i) with kt.V = 0 and V = (d_tau + 2 Hc) B, so
+ * kt_i Sig_ij has the transverse part i kt^2 V_j; hence
+ *  W_j = -i (delta_jl - kt_j kt_l / kt^2) kt_i Sig_il,k / kt^2,
+ *  B_j,k = b_decay B_j,k(previous) + dtau_prev W_j      (bs holds B_k between steps).
  * Newtonian mode: phi_k = -R_k / kt^2, phi_0 = 0, chi = B = 0.
  */
 void or_fourier_solve(int n, const or_solve_params *sp, cplx *Rk /* in: R, out: phi */,
                       cplx *Fk /* 3 N^3: in F, out B */, cplx *Sk /* 6 N^3: in Sig; [0] out chi */,
-                      cplx *hp, cplx *hx, cplx *vp, cplx *vx)
+                      cplx *hp, cplx *hx, cplx *vp, cplx *vx, cplx *bs /* 3 N^3 B_k state, b_space only */)
 {
     long N = n;
     size_t nc = (size_t)n * n * n;
@@ -498,6 +566,8 @@ void or_fourier_solve(int n, const or_solve_params *sp, cplx *Rk /* in: R, out: 
                 if (zero || nyq) {
                     Sk[c] = 0.0;
                     for (int i = 0; i < 3; i++) Fk[i * nc + c] = 0.0;
+                    if (sp->b_space)
+                        for (int i = 0; i < 3; i++) bs[i * nc + c] = 0.0;
                     hp[c] = hx[c] = vp[c] = vx[c] = 0.0;
                     continue;
                 }
@@ -524,9 +594,21 @@ void or_fourier_solve(int n, const or_solve_params *sp, cplx *Rk /* in: R, out: 
                     for (int j = 0; j < 3; j++) kks += kt[i] * kt[j] * S[i][j];
                 Sk[c] = -3.0 / (4.0 * k2 * k2) * kks;
                 /* frame dragging B */
-                cplx F[3] = {Fk[c], Fk[nc + c], Fk[2 * nc + c]};
-                cplx kF = kt[0] * F[0] + kt[1] * F[1] + kt[2] * F[2];
-                for (int i = 0; i < 3; i++) Fk[i * nc + c] = 4.0 * (F[i] - kt[i] * kF / k2) / k2;
+                if (sp->b_space && !sp->b_seed) {
+                    cplx v[3];
+                    for (int l = 0; l < 3; l++) v[l] = kt[0] * S[0][l] + kt[1] * S[1][l] + kt[2] * S[2][l];
+                    cplx kv = kt[0] * v[0] + kt[1] * v[1] + kt[2] * v[2];
+                    for (int j = 0; j < 3; j++) {
+                        cplx W = -I * (v[j] - kt[j] * kv / k2) / k2;
+                        Fk[j * nc + c] = sp->b_decay * bs[j * nc + c] + sp->dtau_prev * W;
+                    }
+                } else {
+                    cplx F[3] = {Fk[c], Fk[nc + c], Fk[2 * nc + c]};
+                    cplx kF = kt[0] * F[0] + kt[1] * F[1] + kt[2] * F[2];
+                    for (int i = 0; i < 3; i++) Fk[i * nc + c] = 4.0 * (F[i] - kt[i] * kF / k2) / k2;
+                }
+                if (sp->b_space)
+                    for (int i = 0; i < 3; i++) bs[i * nc + c] = Fk[i * nc + c];
             }
 }
 
@@ -639,8 +721,9 @@ void or_power_spectrum(int n, const double *rho, double omega_m, int nbins,
 /* ------------------------------------------------------------------------ */
 /* Simulation driver: one full PM step = project -> solve -> kick/drift.     */
 /* ------------------------------------------------------------------------ */
+/* flags: 1 Newtonian limit, 2 full Hamiltonian constraint, 4 B from Eq. spacespace */
 typedef struct {
-    int n, nsteps, newtonian, step;
+    int n, nsteps, newtonian, full_hc, b_space, step;
     long np;
     double omega_m, h0, four_pi_g, mass;
     double *a_n, *dtau, *a_half;
@@ -649,17 +732,20 @@ typedef struct {
     double *phi, *chi, *B;                   /* latest solution: phi_n, chi_n, B_n (3 N^3) */
     double *src;                             /* last sources: R, F(3), Sig(6) */
     cplx *hp, *hx, *vp, *vx;                 /* tensor state (full DFT arrays) */
+    cplx *bs;                                /* B_k between steps (b_space) */
 } or_sim;
 
 or_sim *or_sim_create(int n, long np, double omega_m, double box_mpch, double z_init, double z_final,
-                      int nsteps, int newtonian)
+                      int nsteps, int flags)
 {
     or_sim *s = calloc(1, sizeof(or_sim));
     size_t nc = (size_t)n * n * n;
     s->n = n;
     s->np = np;
     s->nsteps = nsteps;
-    s->newtonian = newtonian;
+    s->newtonian = flags & 1;
+    s->full_hc = !s->newtonian && (flags & 2);
+    s->b_space = !s->newtonian && (flags & 4);
     s->omega_m = omega_m;
     s->h0 = box_mpch / 2997.92458;
     s->four_pi_g = 1.5 * s->h0 * s->h0;
@@ -681,6 +767,7 @@ or_sim *or_sim_create(int n, long np, double omega_m, double box_mpch, double z_
     s->hx = calloc(nc, sizeof(cplx));
     s->vp = calloc(nc, sizeof(cplx));
     s->vx = calloc(nc, sizeof(cplx));
+    s->bs = calloc(3 * nc, sizeof(cplx));
     return s;
 }
 
@@ -689,7 +776,7 @@ void or_sim_destroy(or_sim *s)
     if (!s) return;
     free(s->a_n); free(s->dtau); free(s->a_half); free(s->pos); free(s->mom);
     free(s->phi_prev); free(s->chi_prev); free(s->phi_prev2); free(s->phi); free(s->chi); free(s->B);
-    free(s->src); free(s->hp); free(s->hx); free(s->vp); free(s->vx);
+    free(s->src); free(s->hp); free(s->hx); free(s->vp); free(s->vx); free(s->bs);
     free(s);
 }
 
@@ -705,7 +792,7 @@ void or_sim_schedule(const or_sim *s, double *a_n, double *dtau, double *a_half)
  * B (3 N^3); the tensor state (4 interleaved complex N^3 arrays: h+, hx,
  * h+', hx') is advanced in place. */
 void or_solve_sources(int n, const or_solve_params *sp, const double *R, const double *F, const double *Sig,
-                      double *phi, double *chi, double *B, double *tensor)
+                      double *phi, double *chi, double *B, double *tensor, double *bstate)
 {
     size_t nc = (size_t)n * n * n;
     cplx *Rk = to_spectrum(R, n);
@@ -724,7 +811,7 @@ void or_solve_sources(int n, const or_solve_params *sp, const double *R, const d
         }
     }
     cplx *ts = (cplx *)tensor;
-    or_fourier_solve(n, sp, Rk, Fk, Sk, ts, ts + nc, ts + 2 * nc, ts + 3 * nc);
+    or_fourier_solve(n, sp, Rk, Fk, Sk, ts, ts + nc, ts + 2 * nc, ts + 3 * nc, (cplx *)bstate);
     to_real(Rk, n, phi);
     if (full) {
         to_real(Sk, n, chi);
@@ -742,18 +829,20 @@ void or_solve_sources(int n, const or_solve_params *sp, const double *R, const d
 void or_solve_sources_flat(int n, double a, double hc, double dtau_prev, double dtau_prev2, double dtau,
                            double hc_half, double four_pi_g, double omega_m, int newtonian, int bootstrap,
                            const double *R, const double *F, const double *Sig, double *phi, double *chi,
-                           double *B, double *tensor)
+                           double *B, double *tensor, int b_space, int b_seed, double b_decay, double *bstate)
 {
-    or_solve_params sp = {a, hc, dtau_prev, dtau_prev2, dtau, hc_half, four_pi_g, omega_m, newtonian, bootstrap};
-    or_solve_sources(n, &sp, R, F, Sig, phi, chi, B, tensor);
+    or_solve_params sp = {a, hc, dtau_prev, dtau_prev2, dtau, hc_half, four_pi_g, omega_m, newtonian, bootstrap,
+                          0, b_space, b_seed, b_decay};
+    or_solve_sources(n, &sp, R, F, Sig, phi, chi, B, tensor, bstate);
 }
 
 void or_sources_flat(int n, double a, double hc, double dtau_prev, double dtau_prev2, double four_pi_g,
                      double omega_m, int newtonian, int bootstrap, const double *s00, const double *s0i,
                      const double *sij, const double *phi_prev, const double *chi_prev, const double *phi_prev2,
-                     double *R, double *F, double *Sig)
+                     double *R, double *F, double *Sig, int full_hc)
 {
-    or_solve_params sp = {a, hc, dtau_prev, dtau_prev2, 0.0, 0.0, four_pi_g, omega_m, newtonian, bootstrap};
+    or_solve_params sp = {a, hc, dtau_prev, dtau_prev2, 0.0, 0.0, four_pi_g, omega_m, newtonian, bootstrap,
+                          full_hc, 0, 0, 1.0};
     or_sources(n, &sp, s00, s0i, sij, phi_prev, chi_prev, phi_prev2, R, F, Sig);
 }
 
@@ -777,6 +866,10 @@ static void sim_project_solve(or_sim *s, int k, int bootstrap)
     sp.omega_m = s->omega_m;
     sp.newtonian = s->newtonian;
     sp.bootstrap = bootstrap;
+    sp.full_hc = s->full_hc;
+    sp.b_space = s->b_space;
+    sp.b_seed = (k == 0);
+    sp.b_decay = (k >= 1) ? (s->a_n[k - 1] / a) * (s->a_n[k - 1] / a) : 1.0;
     /* at the bootstrap phi_prev = chi_prev = 0, so the weights carry no potential */
     or_project(n, s->pos, s->mom, s->np, s->mass, a, s->phi_prev, s->chi_prev, s->newtonian, s00, s0i, sij);
     double *R = s->src, *F = s->src + nc, *Sig = s->src + 4 * nc;
@@ -786,7 +879,7 @@ static void sim_project_solve(or_sim *s, int k, int bootstrap)
     memcpy(tensor + 2 * nc, s->hx, sizeof(cplx) * nc);
     memcpy(tensor + 4 * nc, s->vp, sizeof(cplx) * nc);
     memcpy(tensor + 6 * nc, s->vx, sizeof(cplx) * nc);
-    or_solve_sources(n, &sp, R, F, Sig, s->phi, s->chi, s->B, tensor);
+    or_solve_sources(n, &sp, R, F, Sig, s->phi, s->chi, s->B, tensor, (double *)s->bs);
     memcpy(s->hp, tensor, sizeof(cplx) * nc);
     memcpy(s->hx, tensor + 2 * nc, sizeof(cplx) * nc);
     memcpy(s->vp, tensor + 4 * nc, sizeof(cplx) * nc);
@@ -806,6 +899,7 @@ void or_sim_set_particles(or_sim *s, const double *pos, const double *mom)
     memset(s->chi_prev, 0, sizeof(double) * nc);
     memset(s->hp, 0, sizeof(cplx) * nc); memset(s->hx, 0, sizeof(cplx) * nc);
     memset(s->vp, 0, sizeof(cplx) * nc); memset(s->vx, 0, sizeof(cplx) * nc);
+    memset(s->bs, 0, sizeof(cplx) * 3 * nc);
     s->step = 0;
     sim_project_solve(s, 0, 1);
     memcpy(s->phi_prev, s->phi, sizeof(double) * nc);

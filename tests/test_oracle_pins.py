@@ -597,3 +597,158 @@ def test_project_vertex_equals_full_projection():
         out = O.project_vertex(n, v, pos, mom, m, a, php, chp)
         ref = np.concatenate([[s00[v[2], v[1], v[0]]], s0i[:, v[2], v[1], v[0]], sij[:, v[2], v[1], v[0]]])
         assert np.max(np.abs(out - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+# ------------------------------------------- variants: full Hc, B from Eq. spacespace -------
+
+def test_laplacian7_eigenvalue_on_single_mode():
+    n = 12
+    nv = (1, -2, 5)
+    f = mode_field(n, nv, 0.2)
+    assert rel(O.laplacian7(f), -(kt_of(nv, n) ** 2).sum() * f) <= 1e-13
+
+
+def _smooth(n, amp, seed):
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n, n, n))
+    for _ in range(4):
+        nv = rng.integers(-2, 3, size=3)
+        f += amp * rng.uniform(0.3, 1.0) * mode_field(n, nv, rng.uniform(0, 2 * np.pi))
+    return f
+
+
+def test_full_hc_remainder_equals_plain_constraint():
+    """Nl = [plain left side of Eq. fullHc - (3/2) Hc^2] - [Lap phi - 3 Hc phi' - 3 Hc^2 psi], the left side
+    evaluated term by term at 50 digits (exp, squares, no regrouping) on the same discrete Lap and grad."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    n, hc, dt2 = 8, 3.7, 0.013
+    phi = _smooth(n, 0.04, 1)
+    chi = _smooth(n, 0.01, 2)
+    phi2 = phi - dt2 * _smooth(n, 0.3, 3)
+    got = O.hc_remainder(hc, dt2, phi, chi, phi2)
+    lap = lap7(phi)
+    g = [(np.roll(phi, -1, axis=2 - d) - np.roll(phi, 1, axis=2 - d)) * 0.5 * n for d in range(3)]
+    H = mp.mpf(hc)
+    worst = 0.0
+    for idx in [(0, 0, 0), (1, 2, 3), (7, 5, 2), (4, 4, 4), (3, 0, 6), (6, 7, 1)]:
+        p, c, dl = mp.mpf(phi[idx]), mp.mpf(chi[idx]), mp.mpf(lap[idx])
+        ps = p - c
+        dp = (p - mp.mpf(phi2[idx])) / mp.mpf(dt2)
+        g2 = sum(mp.mpf(gd[idx]) ** 2 for gd in g)
+        full = mp.e ** (2 * p) * dl - mp.e ** (2 * p) * g2 / 2 + mp.mpf(3) / 2 * (H - dp) ** 2 * mp.e ** (-2 * ps)
+        lin = dl - 3 * H * dp - 3 * H * H * ps
+        expect = full - mp.mpf(3) / 2 * H * H - lin
+        worst = max(worst, abs(float(expect) - got[idx]) / abs(float(expect)))
+    assert worst <= 1e-12, worst
+
+
+def test_full_hc_predictor_iterated_solves_the_nonlinear_constraint():
+    """The paper's predictor-corrector loop (Sec. 3.1): re-solving with the remainder evaluated on the last
+    solution converges to a phi that satisfies the nonlinear discrete Eq. fullHc (here with phi' = 0)."""
+    n, a, hc, g4, om = 16, 0.5, 1.3, 0.9, 0.31
+    chi = _smooth(n, 0.003, 5)
+    S = _smooth(n, 0.05 * (2 * np.pi) ** 2, 6)           # 4piG a^-2 (S00 - a Omega_m): gives phi ~ 1e-2
+    s00 = a * om + S * a * a / g4
+    z3 = np.zeros((3, n, n, n)); z6 = np.zeros((6, n, n, n))
+    big = 1e30                                          # no time derivative: 3 Hc / dtau -> 0 and phi' -> 0
+    guess = np.zeros((n, n, n))
+    for _ in range(40):
+        R, _, _ = O.sources(n, a, hc, big, big, g4, om, s00, z3, z6, guess, chi, guess, full_hc=True)
+        phi, *_ = O.solve_sources(n, R, a=a, hc=hc, dtau_prev=big, dtau_prev2=big, four_pi_g=g4, omega_m=om)
+        step = np.max(np.abs(phi - guess))
+        guess = phi
+    assert step <= 1e-15
+    psi = phi - chi
+    g2 = sum(((np.roll(phi, -1, axis=ax) - np.roll(phi, 1, axis=ax)) * 0.5 * n) ** 2 for ax in range(3))
+    lhs = (np.exp(2 * phi) * lap7(phi) - 0.5 * np.exp(2 * phi) * g2 + 1.5 * hc * hc * np.exp(-2 * psi)
+           - 1.5 * hc * hc)
+    assert np.max(np.abs(lhs - S)) <= 1e-11 * np.max(np.abs(S))
+    # and the linear solve alone misses it by the size of the remainder
+    R0, _, _ = O.sources(n, a, hc, big, big, g4, om, s00, z3, z6, guess, chi, guess, full_hc=False)
+    phi0, *_ = O.solve_sources(n, R0, a=a, hc=hc, dtau_prev=big, dtau_prev2=big, four_pi_g=g4, omega_m=om)
+    assert rel(phi0, phi) > 1e-3
+
+
+def _vector_mode_sig(n, nv, w, phase=0.0):
+    """Sig_ij = -(kt_i w_j + kt_j w_i) sin(k.x): the spin-1 source of (d_tau + 2Hc) B = w cos(k.x)."""
+    kt = kt_of(nv, n)
+    s = -mode_field(n, nv, phase - np.pi / 2)   # -sin(k.x + phase)
+    T = np.outer(kt, w) + np.outer(w, kt)
+    return _sig_from_tensor(T, s), np.stack([w[i] * mode_field(n, nv, phase) for i in range(3)])
+
+
+def test_space_space_b_from_single_vector_mode():
+    n, dtp, decay = 16, 0.037, 0.81
+    nv, nv2 = (2, -1, 1), (0, 1, 3)
+    kt, kt2 = kt_of(nv, n), kt_of(nv2, n)
+    w = np.cross(kt, [0.3, 1.0, -0.2]); w /= np.linalg.norm(w)
+    v = np.cross(kt2, [1.0, 0.0, 0.0]); v /= np.linalg.norm(v)
+    Sig, Wx = _vector_mode_sig(n, nv, w, 0.4)
+    Bold = np.stack([v[i] * mode_field(n, nv2) for i in range(3)])
+    bstate = np.ascontiguousarray(np.stack([np.fft.fftn(c) for c in Bold]))
+    phi, chi, B, _ = O.solve_sources(n, np.zeros((n, n, n)), None, Sig, dtau=0.01, dtau_prev=dtp, b_space=True,
+                                     b_decay=decay, bstate=bstate)
+    assert rel(B, decay * Bold + dtp * Wx) <= 1e-13
+    assert np.max(np.abs(chi)) <= 1e-15 * np.max(np.abs(Sig))
+    # the state now holds the new B_k
+    assert rel(np.stack([np.fft.ifftn(c).real for c in bstate]), B) <= 1e-13
+
+
+def test_space_space_b_ignores_scalar_and_tensor_sources():
+    n = 16
+    nv = (1, 2, 2)
+    kt = kt_of(nv, n)
+    ep, ex = O.polarisations_kt(nv, kt)
+    f = mode_field(n, nv, 0.7)
+    T = -np.outer(kt, kt) + np.eye(3) * (kt @ kt) / 3.0 + 0.5 * ep - 0.3 * ex
+    phi, chi, B, _ = O.solve_sources(n, np.zeros((n, n, n)), None, _sig_from_tensor(T, f), dtau=0.01,
+                                     dtau_prev=0.05, b_space=True, b_decay=0.9,
+                                     bstate=np.zeros((3, n, n, n), complex))
+    assert np.max(np.abs(B)) <= 1e-15 * (kt @ kt)
+
+
+def test_space_space_b_is_the_rate_of_momentum_constraint_b_for_free_streaming():
+    """Covariant conservation ties the two B equations (Sec. 3.1).  For free-streaming matter with no
+    potentials and no expansion (a = 1, Hc = 0), d/dtau of B from the momentum constraint equals W of
+    Eq. spacespace; on a 32 mesh with a smooth 64^3-particle flow they agree to O(dx^2) (here 1.6 %)."""
+    n, m = 32, 64
+    q = (np.stack(np.meshgrid(*(np.arange(m),) * 3, indexing="ij"), -1).reshape(-1, 3)[:, ::-1] + 0.5) / m
+    x0 = q + 0.02 * np.sin(2 * np.pi * q[:, [1, 2, 0]])
+    u = np.stack([0.3 * np.sin(2 * np.pi * x0[:, 1]) + 0.1 * np.cos(2 * np.pi * (x0[:, 2] + x0[:, 1])),
+                  0.2 * np.sin(2 * np.pi * x0[:, 0]) + 0.15 * np.sin(2 * np.pi * x0[:, 2]),
+                  0.25 * np.cos(2 * np.pi * x0[:, 0] + 0.3)], -1)
+    v = u / np.sqrt(1.0 + (u * u).sum(1))[:, None]
+    z = np.zeros((n, n, n))
+
+    def b_of(x, space):
+        s00, s0i, sij = O.project(n, x % 1.0, u, 1.0 / len(x), 1.0, z, z)
+        R, F, S = O.sources(n, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0, s00, s0i, sij, z, z, z)
+        return O.solve_sources(n, R, F, S, a=1.0, hc=0.0, four_pi_g=1.0, omega_m=1.0, dtau_prev=1.0,
+                               b_space=space, b_decay=0.0, bstate=np.zeros((3, n, n, n), complex))[2]
+
+    d = 1e-3
+    dB = (b_of(x0 + 0.5 * d * v, False) - b_of(x0 - 0.5 * d * v, False)) / d
+    W = b_of(x0, True)
+    assert rel(W, dB) <= 0.03
+
+
+def test_space_space_b_converges_to_momentum_constraint_b_with_resolution():
+    """In the cosmological step the two B solutions differ by discretisation terms that shrink as the mesh
+    is refined (same box, same initial conditions): 32^3 -> 64^3 cuts the difference after two steps > 2x."""
+    from paper_2607_17929_gb300 import ics
+
+    def diff(n):
+        out = []
+        for space in (False, True):
+            s = O.OracleSim(n, n ** 3, OM, BOX, 100.0, 0.0, 100, b_space=space)
+            a_m = O.a_after(s.a_n[0], -0.5 * s.dtau[0], OM, s.h0)
+            pos, mom = ics.zeldovich_ics(n, BOX, OM, 0.67, s.a_n[0], a_m, 1)
+            s.set_particles(pos, mom)
+            s.step()
+            s.step()
+            out.append(np.stack([s.field(c) for c in ("Bx", "By", "Bz")]))
+        return rel(out[1], out[0])
+
+    d32, d64 = diff(32), diff(64)
+    assert d32 / d64 > 2.0, (d32, d64)

@@ -349,6 +349,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -396,8 +398,8 @@ def main():
     d_pos = torch.from_numpy(pos).cuda()
     d_mom = torch.from_numpy(mom).cuda()
 
-    def timed_run(precision, warmup, steps):
-        sim = pm.PM(n, n_part, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, precision, 0, stream)
+    def timed_run(precision, warmup, steps, flags=0):
+        sim = pm.PM(n, n_part, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, precision, flags, stream)
         sim.set_particles(d_pos, d_mom)
         for _ in range(warmup):
             sim.step()
@@ -456,6 +458,20 @@ def main():
         del sim64
     torch.cuda.empty_cache()
 
+    # the solve variants on the same workload (mixed)
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        for name, flags in (("full_hc", pm.PM_FULL_HC), ("b_spacespace", pm.PM_B_SPACESPACE),
+                            ("full_hc+b_spacespace", pm.PM_FULL_HC | pm.PM_B_SPACESPACE)):
+            simv, msv, kernv, _, _ = timed_run(pm.PM_MIXED, 3, args.variant_steps, flags)
+            simv.close()
+            del simv
+            msv = max_over_ranks(msv)
+            variants[name] = {"ms_per_step": round(msv, 3), "value": world * n_part / (msv * 1e-3),
+                              "kernels_ms": {k: round(v, 4) for k, v in kernv.items()}}
+        torch.cuda.empty_cache()
+
     ensemble = None
     if not args.no_ensemble:
         ensemble = ensemble_bench(pm, torch, args.ensemble_steps, 3)
@@ -505,6 +521,7 @@ def main():
             "design_roofline_frac": design_bytes / (ms_max * 1e-3) / 1e9 / peak,
             "roofline": roofline,
             "fp64": fp64,
+            "variants": variants,
             "ensemble": ensemble,
             "e2e": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,

@@ -58,6 +58,21 @@ typedef enum {
 #define PM_NEWTONIAN 1u /* Newtonian limit (Sec. 3.2): project mass only, Poisson equation
                            Lap phi = 4 pi G a^-1 (rho - omega_m), chi = B = h = 0,
                            du/dtau = -a grad phi, dx/dtau = u/a */
+#define PM_FULL_HC 2u   /* full Hamiltonian constraint, Eq. fullHc: the terms that are not linear
+                           in phi, psi join the phi source as R -= Nl, with
+                           Nl = (e^{2phi}-1) Lap phi - 1/2 e^{2phi} |grad phi|^2
+                              + 3/2 [(Hc-phi')^2 e^{-2psi} - Hc^2 + 2 Hc phi' + 2 Hc^2 psi]
+                           evaluated once on phi_{n-1}, psi_{n-1} = phi_{n-1} - chi_{n-1} and
+                           phi' = (phi_{n-1} - phi_{n-2}) / dtau_{n-2} (the predictor of Sec. 3.1,
+                           no corrector iterations); 7-point Lap, centred grad */
+#define PM_B_SPACESPACE 4u /* B_i from the spin-1 part of Eq. spacespace instead of the momentum
+                           constraint: (d_tau + 2 Hc) B_j = W_j with
+                           W_j = -i (delta_jl - kt_j kt_l / kt^2) kt_i Sig_il / kt^2, integrated
+                           as a_n^2 B_n = a_{n-1}^2 B_{n-1} + dtau_{n-1} a_n^2 W_n.  Step 0 takes B
+                           from the momentum constraint to start the integration; after it the
+                           T0i sources F are neither written nor transformed (6 forward FFTs
+                           instead of 9), so pm_get_field of F_x..F_z keeps step 0's values.
+                           Both variants are ignored with PM_NEWTONIAN. */
 
 typedef struct pm_config {
     int32_t n_mesh;    /* N: 2^a 3^b, a >= 3, 8 <= N <= 1024 */
@@ -68,7 +83,7 @@ typedef struct pm_config {
     double z_init;     /* redshift of the first step */
     double z_final;    /* redshift after the last step (< z_init) */
     int32_t precision; /* pm_precision */
-    uint32_t flags;    /* PM_NEWTONIAN or 0 */
+    uint32_t flags;    /* 0 or PM_NEWTONIAN | PM_FULL_HC | PM_B_SPACESPACE */
     void *stream;      /* cudaStream_t to enqueue on; NULL = default stream */
 } pm_config;
 

@@ -130,6 +130,11 @@ StepScalars scalars(const Ctx &c, int k, bool bootstrap)
     s.c_phi_dt = (c.newtonian || bootstrap) ? 0.0 : 3.0 * s.hc / dprev;
     s.c_phi_h2 = c.newtonian ? 0.0 : 3.0 * s.hc * s.hc;
     s.inv_dtau_prev2 = 1.0 / dprev2;
+    s.dtau_prev = dprev;
+    s.full_hc = c.full_hc && !bootstrap && !c.newtonian;
+    s.b_space = c.b_space;
+    s.b_seed = (k == 0);
+    s.b_decay = k >= 1 ? (c.a_n[k - 1] / s.a) * (c.a_n[k - 1] / s.a) : 1.0;
     s.dtau = c.dtau[kk];
     s.dtau_kick = 0.5 * (dprev + c.dtau[kk]);
     s.a_half = c.a_half[kk];
@@ -167,8 +172,21 @@ template <class T> pm_status do_solve(Ctx &c, bool bootstrap)
     void *sp[9], *sr[9];
     spec_ptrs<T>(c, sp);
     src_ptrs<T>(c, sr);
-    const int nf = full ? 9 : 1;
-    fft_forward<T>(c, nf, sr, sp);
+    int nf = full ? 9 : 1;
+    void *fin[9], *fout[9];
+    for (int i = 0; i < 9; i++) {
+        fin[i] = sr[i];
+        fout[i] = sp[i];
+    }
+    if (full && s.b_space && !s.b_seed) {
+        // B from Eq. spacespace: the T0i sources F are not needed, transform R and Sig only
+        for (int i = 1; i < 6; i++) {
+            fin[i] = sr[i + 3];
+            fout[i] = sp[i + 3];
+        }
+        nf = 6;
+    }
+    fft_forward<T>(c, nf, fin, fout);
     CKL("fft_forward");
     launch_solve<T>(c, s);
     CKL("solve");
@@ -248,6 +266,7 @@ template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const do
     CK(cudaMemsetAsync(c.phi[c.iphi_prev], 0, sizeof(T) * c.nc, c.stream));
     CK(cudaMemsetAsync(c.chi, 0, sizeof(T) * c.nc, c.stream));
     CK(cudaMemsetAsync(c.tens, 0, sizeof(typename Cplx<T>::type) * 4 * c.nh, c.stream));
+    if (c.bstate) CK(cudaMemsetAsync(c.bstate, 0, sizeof(typename Cplx<T>::type) * 3 * c.nh, c.stream));
     CK(cudaMemsetAsync(c.dscal, 0, sizeof(double) * 8, c.stream));
     c.step = 0;
     pm_status st = do_project<T>(c, true);
@@ -390,6 +409,7 @@ std::vector<Blob> state_blobs(Ctx &c)
     for (int i = 0; i < 3; i++) b.push_back({c.phi[i], ts * (size_t)c.nc});
     b.push_back({c.chi, ts * (size_t)c.nc});
     b.push_back({c.tens, 2 * ts * 4 * (size_t)c.nh});
+    if (c.bstate) b.push_back({c.bstate, 2 * ts * 3 * (size_t)c.nh});
     b.push_back({c.dscal, sizeof(double) * 8});
     return b;
 }
@@ -526,7 +546,7 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
     if (!valid_n(cfg->n_mesh)) return PM_ERR_UNSUPPORTED_SIZE;
     if (cfg->n_steps < 1 || cfg->n_part < 1 || cfg->n_part >= (int64_t)1 << 31 || !(cfg->box_mpch > 0) ||
         !(cfg->omega_m > 0 && cfg->omega_m <= 1) || !(cfg->z_init > cfg->z_final) || !(cfg->z_final > -1) ||
-        (cfg->precision != PM_FP64 && cfg->precision != PM_MIXED) || (cfg->flags & ~PM_NEWTONIAN))
+        (cfg->precision != PM_FP64 && cfg->precision != PM_MIXED) || (cfg->flags & ~(PM_NEWTONIAN | PM_FULL_HC | PM_B_SPACESPACE)))
         return PM_ERR_INVALID_ARG;
     pm_ctx *ctx = new (std::nothrow) pm_ctx();
     if (!ctx) return PM_ERR_OOM;
@@ -544,6 +564,8 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
     c.np = cfg->n_part;
     c.mixed = cfg->precision == PM_MIXED;
     c.newtonian = (cfg->flags & PM_NEWTONIAN) != 0;
+    c.full_hc = !c.newtonian && (cfg->flags & PM_FULL_HC) != 0;
+    c.b_space = !c.newtonian && (cfg->flags & PM_B_SPACESPACE) != 0;
     c.h0 = cfg->box_mpch / 2997.92458;
     c.four_pi_g = 1.5 * c.h0 * c.h0;
     c.mass = cfg->omega_m / (double)c.np;
@@ -597,6 +619,12 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
             return PM_ERR_OOM;
         }
     }
+    if (c.b_space && cudaMalloc(&c.bstate, 3 * 2 * ts * (size_t)c.nh) != cudaSuccess) {
+        cudaGetLastError();
+        c.bstate = nullptr;
+        pm_destroy(ctx);
+        return PM_ERR_OOM;
+    }
     // tables: ktilde(i) = 2N sin(pi n_i / N), twiddles exp(-2 pi i k / N) (long double on the host)
     {
         std::vector<double> kt(c.N), tw(2 * c.N);
@@ -638,6 +666,7 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
     cudaMemset(c.chi, 0, ts * c.nc);
     cudaMemset(c.B, 0, 3 * ts * c.nc);
     cudaMemset(c.tens, 0, 4 * 2 * ts * c.nh);
+    if (c.bstate) cudaMemset(c.bstate, 0, 3 * 2 * ts * c.nh);
     cudaMemset(c.count, 0, sizeof(int32_t) * c.nc);
     for (auto &row : c.evr)
         for (auto &e : row) cudaEventCreate(&e);
@@ -658,7 +687,7 @@ void pm_destroy(pm_ctx *ctx)
     if (c.stream) cudaStreamSynchronize(c.stream);
     else cudaDeviceSynchronize();
     void *ps[] = {c.part[0], c.part[1], c.count, c.start, c.blocksum, c.phi[0], c.phi[1], c.phi[2], c.chi, c.B,
-                  c.src, c.spec, c.tens, c.ktab, c.tw, c.tw2, c.dscal, c.stage_buf};
+                  c.src, c.spec, c.tens, c.ktab, c.tw, c.tw2, c.dscal, c.stage_buf, c.bstate};
     for (void *p : ps)
         if (p) cudaFree(p);
     for (auto &row : c.evr)

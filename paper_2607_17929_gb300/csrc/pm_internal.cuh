@@ -60,6 +60,11 @@ struct StepScalars {
     double omega_m;
     int newtonian;
     int bootstrap;
+    int full_hc;         // remainder of Eq. fullHc in the phi source (not in the bootstrap)
+    int b_space;         // B from Eq. spacespace
+    int b_seed;          // with b_space: this step takes B from the momentum constraint (step 0)
+    double dtau_prev;    // dtau_{n-1}
+    double b_decay;      // (a_{n-1} / a_n)^2
 };
 
 struct FftPlan {
@@ -85,6 +90,8 @@ struct Ctx {
     int64_t np = 0;
     bool mixed = false;
     bool newtonian = false;
+    bool full_hc = false;       // PM_FULL_HC
+    bool b_space = false;       // PM_B_SPACESPACE
 
     // schedule (host, FP64)
     std::vector<double> a_n, dtau, a_half;
@@ -107,6 +114,7 @@ struct Ctx {
     void *src = nullptr;        // 9 * nc real sources
     void *spec = nullptr;       // 9 * nh complex
     void *tens = nullptr;       // 4 * nh complex tensor state
+    void *bstate = nullptr;     // 3 * nh complex B_k between steps (PM_B_SPACESPACE only)
     void *ktab = nullptr;       // N values of ktilde(n)
     void *tw = nullptr;         // N twiddles exp(-2 pi i k / N)
     void *tw2 = nullptr;        // per-stage twiddles of the compile-time-N passes

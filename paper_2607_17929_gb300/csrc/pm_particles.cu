@@ -74,7 +74,57 @@ template <class T> struct DepParams {
     T c1, c2;        // 3Hc/dtau_{n-1}, 3Hc^2
     T inv_dt2;       // 1/dtau_{n-2}
     T halfN;         // N/2 (centred difference 1/(2 dx))
+    int full_hc;     // R -= Nl, the remainder of Eq. fullHc
+    int write_f;     // F_i is needed (momentum-constraint B)
+    T hc, n2;        // Hc(a_n), N^2 (7-point Laplacian 1/dx^2)
+    double inv_g;    // 1 / (4piG a^-2 N^3): Nl's share of the k = 0 sum
 };
+
+// e^x - 1 - x without cancellation: its Taylor series through x^9 / 9! for small |x| (truncation below
+// 1e-8 relative in FP32 for |x| < 1/2 and below 1e-20 in FP64 for |x| < 1e-2), expm1(x) - x beyond.
+template <class T> __device__ __forceinline__ T expm1_minus_x(T x)
+{
+    constexpr T lim = sizeof(T) == 4 ? T(0.5) : T(1e-2);
+    if (fabs(x) >= lim) return expm1(x) - x;
+    T s = T(1.0 / 362880.0);
+    s = s * x + T(1.0 / 40320.0);
+    s = s * x + T(1.0 / 5040.0);
+    s = s * x + T(1.0 / 720.0);
+    s = s * x + T(1.0 / 120.0);
+    s = s * x + T(1.0 / 24.0);
+    s = s * x + T(1.0 / 6.0);
+    s = s * x + T(0.5);
+    return s * x * x;
+}
+
+// Nonlinear remainder of Eq. fullHc at one vertex, from phi_{n-1} and chi_{n-1} staged with a halo of 1
+// (stride st[d] along axis d) and phi_{n-2}:
+//   Nl = (e^{2phi} - 1) Lap phi - 1/2 e^{2phi} |grad phi|^2
+//      + 3/2 [Hc^2 (e^x - 1 - x) - 2 Hc phi' (e^x - 1) + phi'^2 e^x],  x = -2 psi,
+// the bracket being (Hc - phi')^2 e^{-2psi} - Hc^2 + 2 Hc phi' + 2 Hc^2 psi regrouped so that no term
+// of size Hc^2 cancels.
+template <class T>
+__device__ __forceinline__ T hc_remainder(const T *sphi, const T *schi, int vo, const int (&st)[3], T phi2,
+                                          const DepParams<T> &p)
+{
+    const T ph = sphi[vo];
+    T lap = T(-6) * ph, g2 = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const T up = sphi[vo + st[d]], dn = sphi[vo - st[d]];
+        lap += up + dn;
+        const T g = (up - dn) * p.halfN;
+        g2 += g * g;
+    }
+    lap *= p.n2;
+    const T psi = ph - schi[vo];
+    const T dphi = (ph - phi2) * p.inv_dt2;
+    const T x = T(-2) * psi;
+    const T em = expm1(x);
+    const T e2p = exp(T(2) * ph);
+    return expm1(T(2) * ph) * lap - T(0.5) * e2p * g2 +
+           T(1.5) * (p.hc * p.hc * expm1_minus_x(x) - T(2) * p.hc * dphi * em + dphi * dphi * (em + T(1)));
+}
 
 template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 1024; }
 
@@ -279,6 +329,15 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
         __syncthreads();
     }
 
+    const int64_t go = ((int64_t)(z0 + oz) * N + (y0 + oy)) * N + (x0 + ox);
+    const int vo = (ox + 1) + FLD * ((oy + 1) + FLD * (oz + 1));
+    const int st[3] = {1, FLD, FLD * FLD};
+    T nl = T(0);
+    if (p.full_hc) {
+        nl = hc_remainder<T>(sphi, schi, vo, st, p.phi2[go], p);
+        k0 -= (double)nl * p.inv_g;   // the k = 0 mode carries the mean of -Nl
+    }
+
     // k = 0 excess: block reduction in FP64, one atomic per CTA into a slot
     {
         double v = k0;
@@ -295,15 +354,12 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
     }
 
     // epilogue: assemble the field-equation sources at vertex o
-    const int64_t go = ((int64_t)(z0 + oz) * N + (y0 + oy)) * N + (x0 + ox);
-    const int vo = (ox + 1) + FLD * ((oy + 1) + FLD * (oz + 1));
     const T phc = sphi[vo], chc = schi[vo];
     // R: the uniform background a*Omega_m is removed before rounding
     const T dS = (acc00.hi() - p.rb_hi) + (acc00.lo() - p.rb_lo);
-    reinterpret_cast<T *>(p.out.p[0])[go] = p.G * dS - p.c1 * phc - p.c2 * chc;
+    reinterpret_cast<T *>(p.out.p[0])[go] = p.G * dS - p.c1 * phc - p.c2 * chc - nl;
     if (!full) return;
     T gphi[3], gpsi[3];
-    const int st[3] = {1, FLD, FLD * FLD};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const T dp = (sphi[vo + st[d]] - sphi[vo - st[d]]) * p.halfN;
@@ -312,8 +368,10 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
         gpsi[d] = dp - dc;
     }
     const T dphi = (phc - p.phi2[go]) * p.inv_dt2;
+    if (p.write_f) {
 #pragma unroll
-    for (int d = 0; d < 3; d++) reinterpret_cast<T *>(p.out.p[1 + d])[go] = p.G * acc[d] - dphi * gpsi[d];
+        for (int d = 0; d < 3; d++) reinterpret_cast<T *>(p.out.p[1 + d])[go] = p.G * acc[d] - dphi * gpsi[d];
+    }
     T Q[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -797,6 +855,11 @@ void launch_project(Ctx &c, const StepScalars &s)
     p.c2 = (T)s.c_phi_h2;
     p.inv_dt2 = (T)s.inv_dtau_prev2;
     p.halfN = (T)(0.5 * c.N);
+    p.full_hc = s.full_hc;
+    p.write_f = !(s.b_space && !s.b_seed);
+    p.hc = (T)s.hc;
+    p.n2 = (T)((double)c.N * (double)c.N);
+    p.inv_g = 1.0 / (s.four_pi_g / (s.a * s.a) * n3);
     cudaMemsetAsync(c.dscal + 8, 0, sizeof(double) * NK0SLOTS, c.stream);
     const int ntiles = (c.N / TILE) * (c.N / TILE) * (c.N / TILE);
     k_project<T><<<ntiles, DEP_THREADS, dep_smem<T>(), c.stream>>>(p);

@@ -6,6 +6,10 @@
 //   B_i,k = 4 (delta_ij - kt_i kt_j / kt^2) F_j,k / kt^2    (Eq. momentumcontraint, spin-1 part)
 //   h_A   : h'' + 2Hc h' + kt^2 h = e^A_ij Sig_ij, one implicit-midpoint step
 //
+// or, with B from the spin-1 part of Eq. spacespace ((d_tau + 2Hc) B_j = W_j, d_i -> i kt_i):
+//   W_j = -i (delta_jl - kt_j kt_l / kt^2) kt_i Sig_il,k / kt^2
+//   B_j,k = (a_{n-1} / a_n)^2 B_j,k(previous step) + dtau_{n-1} W_j      (backward Euler in a^2 B)
+//
 // with kt_i = 2N sin(pi n_i / N), so kt^2 is the eigenvalue of minus the
 // 7-point Laplacian.  The k = 0 mode of phi comes from the FP64 particle sum
 // of the projection; chi, B and h vanish at k = 0 and on Nyquist modes.
@@ -28,6 +32,9 @@ template <class T> struct SolveParams {
     int full, newtonian, bootstrap;
     double four_pi_g_a2, c1, c2;   // FP64 copies for the k = 0 mode
     T cphi, inv_n3, hc_half, dtau;
+    void *bstate;      // 3 half spectra of B_k (unnormalised), B from Eq. spacespace only
+    int b_space, b_seed;
+    T b_decay, dtau_prev;
 };
 
 template <class T>
@@ -78,6 +85,11 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
         for (int c = 1; c <= 4; c++) S[c * nh + e] = z;
 #pragma unroll
         for (int c = 0; c < 4; c++) H[c * nh + e] = z;
+        if (p.b_space) {
+            C *BS = reinterpret_cast<C *>(p.bstate);
+#pragma unroll
+            for (int c = 0; c < 3; c++) BS[c * nh + e] = z;
+        }
         return;
     }
     // trace-free Sig as a symmetric matrix (Sig_zz = -Sig_xx - Sig_yy)
@@ -156,18 +168,46 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
         S[4 * nh + e] = chi;
     }
     // frame dragging B (written over F)
-    {
+    if (p.b_space && !p.b_seed) {
+        C *BS = reinterpret_cast<C *>(p.bstate);
+        C v[3];
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            v[l].x = kt[0] * Sm[0][l].x + kt[1] * Sm[1][l].x + kt[2] * Sm[2][l].x;
+            v[l].y = kt[0] * Sm[0][l].y + kt[1] * Sm[1][l].y + kt[2] * Sm[2][l].y;
+        }
+        C kv;
+        kv.x = kt[0] * v[0].x + kt[1] * v[1].x + kt[2] * v[2].x;
+        kv.y = kt[0] * v[0].y + kt[1] * v[1].y + kt[2] * v[2].y;
+        const T ik2 = T(1) / k2;
+        const T w = p.dtau_prev * ik2;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            // dtau W_j = dtau (-i) (v_j - kt_j kv / kt^2) / kt^2
+            const T px = v[j].x - kt[j] * kv.x * ik2, py = v[j].y - kt[j] * kv.y * ik2;
+            C b = BS[j * nh + e];
+            b.x = p.b_decay * b.x + w * py;
+            b.y = p.b_decay * b.y - w * px;
+            BS[j * nh + e] = b;
+            b.x *= p.inv_n3;
+            b.y *= p.inv_n3;
+            S[(1 + j) * nh + e] = b;
+        }
+    } else {
         const C F[3] = {S[nh + e], S[2 * nh + e], S[3 * nh + e]};
         C kF;
         kF.x = kt[0] * F[0].x + kt[1] * F[1].x + kt[2] * F[2].x;
         kF.y = kt[0] * F[0].y + kt[1] * F[1].y + kt[2] * F[2].y;
         const T ik2 = T(1) / k2;
-        const T f = T(4) * ik2 * p.inv_n3;
+        const T f = T(4) * ik2;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             C b;
             b.x = f * (F[i].x - kt[i] * kF.x * ik2);
             b.y = f * (F[i].y - kt[i] * kF.y * ik2);
+            if (p.b_space) reinterpret_cast<C *>(p.bstate)[i * nh + e] = b;  // seeds the integration
+            b.x *= p.inv_n3;
+            b.y *= p.inv_n3;
             S[(1 + i) * nh + e] = b;
         }
     }
@@ -226,6 +266,11 @@ void launch_solve(Ctx &c, const StepScalars &s)
     p.inv_n3 = (T)(1.0 / (double)c.nc);
     p.hc_half = (T)s.hc_half;
     p.dtau = (T)s.dtau;
+    p.bstate = c.bstate;
+    p.b_space = s.b_space && c.bstate != nullptr;
+    p.b_seed = s.b_seed;
+    p.b_decay = (T)s.b_decay;
+    p.dtau_prev = (T)s.dtau_prev;
     k_solve<T><<<(unsigned)((c.nh + 255) / 256), 256, 0, c.stream>>>(p);
     c.launches++;
 }

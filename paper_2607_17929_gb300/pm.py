@@ -19,7 +19,7 @@ PM_OK, PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED_SIZE, PM_ERR_OOM, PM_ERR_CUDA, PM_
 STATUS_NAMES = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_UNSUPPORTED_SIZE", 3: "PM_ERR_OOM",
                 4: "PM_ERR_CUDA", 5: "PM_ERR_TIMEOUT", 6: "PM_ERR_STATE"}
 PM_FP64, PM_MIXED = 0, 1
-PM_NEWTONIAN = 1
+PM_NEWTONIAN, PM_FULL_HC, PM_B_SPACESPACE = 1, 2, 4
 FIELDS = {"phi": 0, "chi": 1, "Bx": 2, "By": 3, "Bz": 4, "R": 5, "Fx": 6, "Fy": 7, "Fz": 8,
           "Sxx": 9, "Sxy": 10, "Sxz": 11, "Syy": 12, "Syz": 13}
 TENSORS = {"h+": 0, "hx": 1, "h+'": 2, "hx'": 3}

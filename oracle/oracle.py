@@ -66,6 +66,10 @@ def lib():
         L.or_sim_set_particles.argtypes = [C.c_void_p, _dp, _dp]
         L.or_sim_step.restype = C.c_int
         L.or_sim_step.argtypes = [C.c_void_p]
+        L.or_sim_solve.restype = C.c_int
+        L.or_sim_solve.argtypes = [C.c_void_p]
+        L.or_sim_update.restype = C.c_int
+        L.or_sim_update.argtypes = [C.c_void_p, C.c_void_p]
         L.or_sim_get_field.argtypes = [C.c_void_p, C.c_int, _dp]
         L.or_sim_get_tensor.argtypes = [C.c_void_p, C.c_int, _dp]
         L.or_sim_get_particles.argtypes = [C.c_void_p, _dp, _dp]
@@ -253,6 +257,17 @@ class OracleSim:
 
     def step(self):
         return lib().or_sim_step(self._h)
+
+    def solve(self):
+        """First half of a step: project and solve (fields of step n)."""
+        return lib().or_sim_solve(self._h)
+
+    def update(self, corr=None):
+        """Second half: kick (plus the extra kick of a force correction corr [3][n][n][n]) and drift."""
+        if corr is None:
+            return lib().or_sim_update(self._h, None)
+        c = np.ascontiguousarray(corr, dtype=np.float64).reshape(-1)
+        return lib().or_sim_update(self._h, c.ctypes.data_as(C.c_void_p))
 
     @property
     def step_index(self):

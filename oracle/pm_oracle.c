@@ -907,15 +907,37 @@ void or_sim_set_particles(or_sim *s, const double *pos, const double *mom)
     memset(s->chi_prev, 0, sizeof(double) * nc);
 }
 
-/* One full step n: project at x_n, solve for phi_n, chi_n, B_n, h, then kick
- * and drift.  Returns the new step index, or -1 past the end of the schedule. */
-int or_sim_step(or_sim *s)
+/* First half of step n: project at x_n and solve for phi_n, chi_n, B_n, h. */
+int or_sim_solve(or_sim *s)
+{
+    int k = s->step;
+    if (k >= s->nsteps) return -1;
+    sim_project_solve(s, k, 0);
+    return k;
+}
+
+/* Second half of step n: kick and drift, then rotate the potentials.  With
+ * corr != NULL (3 N^3, components x, y, z of an additive force correction c
+ * on the mesh), every particle first receives the extra kick
+ *   u += dtau_kick * f * c(x_p)   (CIC value; f = a_n in the Newtonian mode,
+ *                                  f = E = sqrt(a_n^2 + u^2) otherwise),
+ * i.e. c corrects the force -grad psi of the kick.  Returns the new step index. */
+int or_sim_update(or_sim *s, const double *corr)
 {
     int k = s->step;
     if (k >= s->nsteps) return -1;
     size_t nc = (size_t)s->n * s->n * s->n;
-    sim_project_solve(s, k, 0);
     double dtau_kick = 0.5 * ((k >= 1 ? s->dtau[k - 1] : s->dtau[0]) + s->dtau[k]);
+    if (corr) {
+        double a = s->a_n[k];
+        for (long p = 0; p < s->np; p++) {
+            double *u = s->mom + 3 * p;
+            double f = s->newtonian ? a : sqrt(a * a + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            double c[3];
+            for (int i = 0; i < 3; i++) c[i] = or_cic_value(corr + i * nc, s->n, s->pos + 3 * p);
+            for (int i = 0; i < 3; i++) u[i] += dtau_kick * f * c[i];
+        }
+    }
     or_kick_drift(s->n, s->pos, s->mom, s->np, s->a_n[k], s->a_half[k], dtau_kick, s->dtau[k], s->newtonian,
                   s->phi, s->chi, s->B);
     memcpy(s->phi_prev2, s->phi_prev, sizeof(double) * nc);
@@ -923,6 +945,14 @@ int or_sim_step(or_sim *s)
     memcpy(s->chi_prev, s->chi, sizeof(double) * nc);
     s->step = k + 1;
     return s->step;
+}
+
+/* One full step n: or_sim_solve then or_sim_update without correction.
+ * Returns the new step index, or -1 past the end of the schedule. */
+int or_sim_step(or_sim *s)
+{
+    if (or_sim_solve(s) < 0) return -1;
+    return or_sim_update(s, NULL);
 }
 
 /* Field ids: 0 phi, 1 chi, 2..4 B_x..B_z, 5 R, 6..8 F, 9..14 Sig (xx,xy,xz,yy,yz,zz) */

@@ -275,6 +275,83 @@ pm_status pm_ensemble_stream(pm_ensemble *e, void **stream);
  * *n_streams receives it.  Each trial advances every box by one step. */
 pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams);
 
+/* ------------------------------------------------------------------------
+ * Learned sub-mesh force correction.  The paper has no learned component:
+ * this is an optional addition to the Newtonian-mode step.  A 3^3 periodic
+ * convolutional network (2 -> 16 -> 16 -> 16 -> 3 channels, ReLU between
+ * layers, BF16 weights and activations, FP32 accumulation) maps
+ *   x0 = delta = R / kappa,  x1 = phi N^2 / kappa,   kappa = 4piG Omega_m / a,
+ * of a solved context to y (3 channels), and the next pm_update kicks every
+ * particle with the extra force c = (kappa / N) y interpolated by CIC:
+ *   u += dtau_kick * a_n * c(x_p)           (Newtonian mode).
+ * Trained on targets y* = (R_2(F_2N) - F_N) N / kappa: the full-weighting
+ * restriction of the force -grad phi of the same particles on a mesh twice
+ * as fine, minus the force on the context's mesh (centred differences).
+ *
+ * Layouts (device memory): activations BF16 [cell][16] (cell = (z N + y) N + x,
+ * channels beyond the used ones zero); targets and outputs FP32 [cell][8]
+ * (channels 0..2 used); parameters FP32, per layer W [27][16 c_out][16 c_in]
+ * with d = 9 (dz+1) + 3 (dy+1) + (dx+1), then b [16], padded entries zero
+ * (pm_net_param_count() floats in all).  N must be a multiple of 8.
+ * ------------------------------------------------------------------------ */
+typedef struct pm_net pm_net;
+
+enum { PM_NET_INPUT = 0, PM_NET_OUTPUT = 1, PM_NET_GRAD = 2 };
+
+int64_t pm_net_param_count(void);
+
+/* Network with buffers for an n_mesh^3 mesh, weights He-initialised from `seed`
+ * (SplitMix64 + Box-Muller; last layer scaled by 0.1), biases zero.
+ * Errors: UNSUPPORTED_SIZE (n_mesh not a multiple of 8 in [8, 1024]), OOM. */
+pm_status pm_net_create(int32_t n_mesh, uint64_t seed, void *stream, pm_net **out);
+void pm_net_destroy(pm_net *net);
+const char *pm_net_last_error(const pm_net *net);
+
+/* FP32 parameters in or out (host or device pointer); set also resets Adam. */
+pm_status pm_net_set_params(pm_net *net, const float *params);
+pm_status pm_net_get_params(pm_net *net, float *params);
+
+/* Device address of an internal buffer: PM_NET_INPUT (BF16 [cell][16]),
+ * PM_NET_OUTPUT (FP32 [cell][8]), PM_NET_GRAD (FP32 parameter gradient,
+ * same layout as the parameters; accumulated by pm_net_backward, cleared by
+ * pm_net_adam).  Owned by the network. */
+pm_status pm_net_buffer(pm_net *net, int32_t which, void **ptr);
+
+/* Inputs x0, x1 from a context after pm_solve (Newtonian mode, same n_mesh). */
+pm_status pm_net_features(pm_net *net, pm_ctx *ctx);
+/* Training target (FP32 [cell][8], device) from a solved context and a
+ * solved context of the same particles on a mesh twice as fine, solved at
+ * the same scale factor (same box, Omega_m, particle count and precision). */
+pm_status pm_net_target(pm_net *net, pm_ctx *coarse, pm_ctx *fine, float *target);
+/* Forward pass: input buffer -> output buffer. */
+pm_status pm_net_forward(pm_net *net);
+/* Forward, MSE loss against `target` (mean over cells and the 3 channels;
+ * *loss receives it if non-NULL, which synchronises) and backward into the
+ * gradient buffer. */
+pm_status pm_net_backward(pm_net *net, const float *target, double *loss);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) with learning rate lr. */
+pm_status pm_net_adam(pm_net *net, float lr);
+pm_status pm_net_train_step(pm_net *net, const float *target, float lr, double *loss);
+/* Features + forward on a solved context, and attach the output as the
+ * context's force correction for the following pm_update. */
+pm_status pm_net_apply(pm_net *net, pm_ctx *ctx);
+/* Attach (or with NULL detach) a force correction FP32 [cell][8] in force
+ * units; every later pm_update kicks it in (factor a_n in the Newtonian mode,
+ * E = sqrt(a_n^2 + u^2) otherwise).  Not owned by the context. */
+pm_status pm_set_correction(pm_ctx *ctx, const float *corr);
+
+/* The layer kernels on caller buffers (device pointers, stream as above):
+ * y = act(conv(x, w) + bias) with x BF16 [n^3][16], w BF16 [27][16][16]
+ * ([d][c_out][c_in]), bias FP32 [16] or NULL; c_out = 16 writes BF16
+ * [n^3][16] (relu 0/1), c_out = 8 writes FP32 [n^3][8] (relu 0) from the first
+ * 8 output channels of w.  The input gradient of a layer is this convolution
+ * with w'[26 - d][c_in][c_out] = w[d][c_out][c_in]. */
+pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float *bias, int32_t c_out, int32_t relu,
+                            void *y, void *stream);
+/* dw[d][c_out][c_in] += sum over cells of g[cell][c_out] x[cell + d][c_in]
+ * (x, g BF16 [n^3][16]; dw FP32 [27][16][16], accumulated with atomics). */
+pm_status pm_conv3d_backward_weight(int32_t n, const void *x, const void *g, float *dw, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

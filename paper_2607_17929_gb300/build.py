@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libpm.so")
-SOURCES = ["pm_api.cu", "pm_ensemble.cu", "pm_fft.cu", "pm_noalloc.cu", "pm_particles.cu", "pm_solve.cu"]
+SOURCES = ["pm_api.cu", "pm_ensemble.cu", "pm_fft.cu", "pm_net.cu", "pm_noalloc.cu", "pm_particles.cu", "pm_solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++20", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -206,6 +206,8 @@ template <class T> pm_status do_solve(Ctx &c, bool bootstrap)
 template <class T> pm_status do_update(Ctx &c)
 {
     StepScalars s = scalars(c, c.step, false);
+    launch_corr_kick<T>(c, s);
+    CKL("corr_kick");
     launch_kick_drift<T>(c, s);
     CKL("kick_drift");
     c.mark(EV_KICK);

@@ -115,6 +115,8 @@ struct Ctx {
     void *spec = nullptr;       // 9 * nh complex
     void *tens = nullptr;       // 4 * nh complex tensor state
     void *bstate = nullptr;     // 3 * nh complex B_k between steps (PM_B_SPACESPACE only)
+    void *corr = nullptr;       // force correction FP32 [cell][8] (channels 0..2) kicked in by pm_update; not owned
+    float corr_scale = 1.f;     // force units per unit of corr
     void *ktab = nullptr;       // N values of ktilde(n)
     void *tw = nullptr;         // N twiddles exp(-2 pi i k / N)
     void *tw2 = nullptr;        // per-stage twiddles of the compile-time-N passes
@@ -160,6 +162,8 @@ template <class T>
 void launch_kick_drift(Ctx &c, const StepScalars &s);
 template <class T>
 void launch_sort(Ctx &c);
+template <class T>
+void launch_corr_kick(Ctx &c, const StepScalars &s);
 template <class T>
 void launch_load_particles(Ctx &c, const double *d_pos, const double *d_mom, int64_t first, int64_t count);
 template <class T>

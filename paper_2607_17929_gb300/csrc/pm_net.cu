@@ -1,0 +1,740 @@
+// Learned sub-mesh force correction: a 3^3 periodic convolutional network
+// (2 -> 16 -> 16 -> 16 -> 3 channels, ReLU between layers) that maps the
+// density contrast and potential of a PM step to an additive correction of
+// the mesh force, its training (MSE, Adam) and the extra kick it gives.
+//
+// Layout.  Activations and gradients are BF16, channels-last [cell][16]
+// (cell = (z N + y) N + x); the network output and the targets are FP32
+// [cell][8] (channels 0..2 used).  Weights are BF16 [27][c_out = 16][c_in = 16]
+// with the offset index d = 9 (dz + 1) + 3 (dy + 1) + (dx + 1); the first
+// layer's inputs and the last layer's outputs are zero-padded to 16, so every
+// layer is one 16 x 16 contraction per offset.
+//
+// Convolution as an implicit GEMM on the tensor cores (mma.sync m16n8k16,
+// BF16 in, FP32 accumulate).  One CTA computes an 8^3 tile of cells: the
+// 10^3 halo of input cells (32 B each) and the weights sit in shared memory,
+// each of the 8 warps owns one z-slice of the tile (64 cells = 4 m16 blocks
+// x 2 n8 blocks of output channels), and the K dimension runs over the 27
+// offsets x 16 input channels, one k16 step per offset.  Rows of 32 B are
+// stored with their two 16-byte halves swapped every 4 cells, so the eight
+// row addresses of an ldmatrix phase hit eight different bank groups.
+//
+// Backward: the input gradient is the same convolution with the offsets
+// reversed and the weights transposed; the weight gradient is a second GEMM
+// (M = c_out, N = c_in, K = cells) per offset, accumulated by persistent CTAs
+// and added to global memory once per CTA.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+namespace {
+
+constexpr int NL = 4;                       // layers
+constexpr int CH = 16;                      // padded channels
+constexpr int NOFF = 27;
+constexpr int WSZ = NOFF * CH * CH;         // weights of one layer (padded)
+constexpr int PSZ = WSZ + CH;               // + bias
+constexpr int NPARAM = NL * PSZ;
+constexpr int CIN[NL] = {2, 16, 16, 16};
+constexpr int COUT[NL] = {16, 16, 16, 3};
+constexpr int TT = 8;                       // tile side
+constexpr int HT = TT + 2;                  // halo tile side
+constexpr int NH = HT * HT * HT;            // 1000 halo cells
+constexpr int CONV_THREADS = 256;
+
+__device__ __forceinline__ int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// 16-byte chunk q (0: channels 0-7, 1: channels 8-15) of row r in a swizzled [rows][2] uint4 array
+__device__ __forceinline__ int swz(int r, int q) { return 2 * r + (q ^ ((r >> 2) & 1)); }
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldm_x4(unsigned addr, unsigned (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldm_x4_t(unsigned addr, unsigned (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+// D += A (m16 x k16, row) * B (k16 x n8, col), BF16 inputs, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// load the 10^3 halo of an 8^3 tile (BF16 [cell][16], 2 x 16 B per cell) into swizzled shared memory
+__device__ __forceinline__ void load_halo(uint4 *sx, const uint4 *x, int n, int x0, int y0, int z0)
+{
+    for (int i = threadIdx.x; i < 2 * NH; i += blockDim.x) {
+        const int h = i >> 1, q = i & 1;
+        const int hx = h % HT, hy = (h / HT) % HT, hz = h / (HT * HT);
+        const int64_t g = ((int64_t)wrapn(z0 - 1 + hz, n) * n + wrapn(y0 - 1 + hy, n)) * n + wrapn(x0 - 1 + hx, n);
+        sx[swz(h, q)] = x[2 * g + q];
+    }
+}
+
+// y = act(conv(x, w) + b): one 8^3 tile per CTA.  NB = 2 (16 outputs) or 1 (8 outputs).
+template <int NB, bool RELU, bool OUTF32>
+__global__ void __launch_bounds__(CONV_THREADS, 3)
+    k_conv(const uint4 *__restrict__ x, const uint4 *__restrict__ w, const float *__restrict__ bias, void *y, int n)
+{
+    __shared__ uint4 sx[2 * NH];          // 32000 B
+    __shared__ uint4 sw[2 * NOFF * CH];   // 13824 B
+    const int nt = n / TT, b = blockIdx.x;
+    const int x0 = (b % nt) * TT, y0 = ((b / nt) % nt) * TT, z0 = (b / (nt * nt)) * TT;
+    load_halo(sx, x, n, x0, y0, z0);
+    for (int i = threadIdx.x; i < 2 * NOFF * CH; i += blockDim.x) sw[swz(i >> 1, i & 1)] = w[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[4][NB][4] = {};
+    // per-lane row of the A fragments: cell (cx, cy = 2j + r / 8, cz = warp), chunk = lane / 16
+    const int r = lane & 15, ach = lane >> 4;
+    const int acx = r & 7, acy = r >> 3;
+    // per-lane row of the B fragments: output channel co = (lane / 16) * 8 + lane % 8, chunk (lane / 8) % 2
+    const int bco = ((lane >> 4) << 3) + (lane & 7), bch = (lane >> 3) & 1;
+#pragma unroll 1
+    for (int d = 0; d < NOFF; d++) {
+        const int dz = d / 9 - 1, dy = (d / 3) % 3 - 1, dx = d % 3 - 1;
+        unsigned bf[4];
+        ldm_x4(smem_u32(&sw[swz(d * CH + bco, bch)]), bf);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int h = ((warp + dz + 1) * HT + (2 * j + acy + dy + 1)) * HT + (acx + dx + 1);
+            unsigned af[4];
+            ldm_x4(smem_u32(&sx[swz(h, ach)]), af);
+            mma_bf16(acc[j][0], af, bf[0], bf[1]);
+            if (NB == 2) mma_bf16(acc[j][NB - 1], af, bf[2], bf[3]);
+        }
+    }
+    // epilogue: rows g (cy = 2j) and g + 8 (cy = 2j + 1) of each m16 block, channels nb*8 + 2t, +1
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int hf = 0; hf < 2; hf++) {
+            const int64_t cell = ((int64_t)(z0 + warp) * n + (y0 + 2 * j + hf)) * n + (x0 + g);
+#pragma unroll
+            for (int nb = 0; nb < NB; nb++) {
+                const int ch = nb * 8 + 2 * t;
+                float v0 = acc[j][nb][2 * hf] + (bias ? bias[ch] : 0.f);
+                float v1 = acc[j][nb][2 * hf + 1] + (bias ? bias[ch + 1] : 0.f);
+                if (RELU) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                if (OUTF32) {
+                    reinterpret_cast<float2 *>(y)[(cell * (NB * 8) + ch) >> 1] = make_float2(v0, v1);
+                } else {
+                    reinterpret_cast<__nv_bfloat162 *>(y)[(cell * CH + ch) >> 1] = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+}
+
+// dw[d][co][ci] += sum_cells g[cell][co] x[cell + d][ci]; persistent CTAs over 8^3 tiles.
+// Warp w owns the offsets d = w, w + 8, w + 16 (and w + 24 for w < 3).
+__global__ void __launch_bounds__(CONV_THREADS, 2)
+    k_conv_dw(const uint4 *__restrict__ x, const uint4 *__restrict__ gr, float *dw, int n)
+{
+    __shared__ uint4 sx[2 * NH];          // 32000 B
+    __shared__ uint4 sg[2 * TT * TT * TT];  // 16384 B
+    const int nt = n / TT, ntiles = nt * nt * nt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[4][2][4] = {};
+    // ldmatrix.trans lane roles.  G (A operand, rows = cells, chunk = co half): matrix mi = lane / 8
+    // covers cells (mi / 2) * 8 + lane % 8 of the k16 step, chunk mi % 2.
+    const int ga_cell = ((lane >> 4) << 3) + (lane & 7), ga_ch = (lane >> 3) & 1;
+    // X (B operand): cells ((lane / 8) % 2) * 8 + lane % 8, chunk (lane / 16) = n8 block.
+    const int xb_cell = (((lane >> 3) & 1) << 3) + (lane & 7), xb_ch = lane >> 4;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % nt) * TT, y0 = ((tile / nt) % nt) * TT, z0 = (tile / (nt * nt)) * TT;
+        __syncthreads();
+        load_halo(sx, x, n, x0, y0, z0);
+        for (int i = threadIdx.x; i < 2 * TT * TT * TT; i += blockDim.x) {
+            const int m = i >> 1, q = i & 1;
+            const int cx = m & 7, cy = (m >> 3) & 7, cz = m >> 6;
+            const int64_t gc = ((int64_t)(z0 + cz) * n + (y0 + cy)) * n + (x0 + cx);
+            sg[swz(m, q)] = gr[2 * gc + q];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int s = 0; s < 32; s++) {
+            // k16 step s: tile cells m = 16 s + k, i.e. cz = s / 4, cy = 2 (s % 4) + k / 8, cx = k % 8
+            unsigned af[4];
+            ldm_x4_t(smem_u32(&sg[swz(16 * s + ga_cell, ga_ch)]), af);
+            const int kcx = xb_cell & 7, kcy = 2 * (s & 3) + (xb_cell >> 3), kcz = s >> 2;
+#pragma unroll
+            for (int o = 0; o < 4; o++) {
+                const int d = warp + 8 * o;
+                if (d < NOFF) {
+                    const int dz = d / 9 - 1, dy = (d / 3) % 3 - 1, dx = d % 3 - 1;
+                    const int h = ((kcz + dz + 1) * HT + (kcy + dy + 1)) * HT + (kcx + dx + 1);
+                    unsigned bf[4];
+                    ldm_x4_t(smem_u32(&sx[swz(h, xb_ch)]), bf);
+                    // x4.trans matrices: 0 = (cells 0-7, chunk 0), 1 = (cells 8-15, chunk 0),
+                    // 2 = (cells 0-7, chunk 1), 3 = (cells 8-15, chunk 1)
+                    mma_bf16(acc[o][0], af, bf[0], bf[1]);
+                    mma_bf16(acc[o][1], af, bf[2], bf[3]);
+                }
+            }
+        }
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int o = 0; o < 4; o++) {
+        const int d = warp + 8 * o;
+        if (d >= NOFF) continue;
+#pragma unroll
+        for (int nb = 0; nb < 2; nb++) {
+            float *base = dw + (size_t)d * CH * CH;
+            const int ci = nb * 8 + 2 * t;
+            atomicAdd(&base[g * CH + ci], acc[o][nb][0]);
+            atomicAdd(&base[g * CH + ci + 1], acc[o][nb][1]);
+            atomicAdd(&base[(g + 8) * CH + ci], acc[o][nb][2]);
+            atomicAdd(&base[(g + 8) * CH + ci + 1], acc[o][nb][3]);
+        }
+    }
+}
+
+// G = g * (y > 0) (mask != 0) or G = g, and db[c] += sum_cells G[cell][c]
+__global__ void k_mask(const __nv_bfloat16 *gin, const __nv_bfloat16 *yact, __nv_bfloat16 *gout, float *db,
+                       int64_t ncell, int mask)
+{
+    __shared__ float sdb[CONV_THREADS / 32][CH];
+    float part = 0.f;   // this thread's channel is fixed: c = threadIdx.x % 16
+    const int c = threadIdx.x & (CH - 1);
+    const int64_t total = ncell * CH;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = __bfloat162float(gin[i]);
+        if (mask && !(__bfloat162float(yact[i]) > 0.f)) v = 0.f;
+        const __nv_bfloat16 vb = __float2bfloat16_rn(v);
+        gout[i] = vb;
+        part += __bfloat162float(vb);
+    }
+    // lanes c and c + 16 of a warp hold the same channel
+    part += __shfl_down_sync(0xffffffffu, part, 16);
+    if ((threadIdx.x & 31) < CH) sdb[threadIdx.x >> 5][c] = part;
+    __syncthreads();
+    if (threadIdx.x < CH) {
+        float s = 0.f;
+        for (int w = 0; w < CONV_THREADS / 32; w++) s += sdb[w][threadIdx.x];
+        atomicAdd(&db[threadIdx.x], s);
+    }
+}
+
+// loss = mean over cells and channels 0..2 of (out - tgt)^2; G = 2 (out - tgt) / (3 ncell) as BF16 [cell][16]
+__global__ void k_loss(const float *out, const float *tgt, __nv_bfloat16 *gr, double *loss, int64_t ncell)
+{
+    __shared__ double sl[CONV_THREADS / 32];
+    double part = 0.0;
+    const float sc = 2.f / (3.f * (float)ncell);
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        __nv_bfloat162 gv[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) gv[k] = __floats2bfloat162_rn(0.f, 0.f);
+        float d[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            d[a] = out[8 * c + a] - tgt[8 * c + a];
+            part += (double)d[a] * (double)d[a];
+        }
+        gv[0] = __floats2bfloat162_rn(sc * d[0], sc * d[1]);
+        gv[1] = __floats2bfloat162_rn(sc * d[2], 0.f);
+        uint4 *dst = reinterpret_cast<uint4 *>(gr + 16 * c);
+        dst[0] = *reinterpret_cast<uint4 *>(&gv[0]);
+        dst[1] = *reinterpret_cast<uint4 *>(&gv[4]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < CONV_THREADS / 32; w++) s += sl[w];
+        atomicAdd(loss, s / (3.0 * (double)ncell));
+    }
+}
+
+// BF16 copies of the FP32 master parameters: forward weights [l][27][co][ci], transposed and
+// offset-reversed weights [l][27][ci][co] (input-gradient convolution), FP32 biases
+__global__ void k_pack(const float *theta, __nv_bfloat16 *wf, __nv_bfloat16 *wt, float *bias)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPARAM) return;
+    const int l = i / PSZ, e = i % PSZ;
+    if (e >= WSZ) {
+        bias[l * CH + (e - WSZ)] = theta[i];
+        return;
+    }
+    const int d = e / (CH * CH), co = (e / CH) % CH, ci = e % CH;
+    const __nv_bfloat16 v = __float2bfloat16_rn(theta[i]);
+    wf[(size_t)l * WSZ + e] = v;
+    wt[(size_t)l * WSZ + ((NOFF - 1 - d) * CH + ci) * CH + co] = v;
+}
+
+// one Adam step (Kingma & Ba 2015) on every parameter; zeroes the gradient for the next step
+__global__ void k_adam(float *theta, float *grad, float *m, float *v, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPARAM) return;
+    const float g = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    grad[i] = 0.f;
+}
+
+// network inputs from a solved context: channel 0 = delta = R / kappa, channel 1 = phi N^2 / kappa
+template <class T>
+__global__ void k_features(const T *R, const T *phi, double inv_kappa, double n2, __nv_bfloat16 *x, int64_t ncell)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    __nv_bfloat162 v[8];
+    v[0] = __floats2bfloat162_rn((float)((double)R[c] * inv_kappa), (float)((double)phi[c] * n2 * inv_kappa));
+#pragma unroll
+    for (int k = 1; k < 8; k++) v[k] = __floats2bfloat162_rn(0.f, 0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(x + 16 * c);
+    dst[0] = *reinterpret_cast<uint4 *>(&v[0]);
+    dst[1] = *reinterpret_cast<uint4 *>(&v[4]);
+}
+
+// target = (restriction of the fine-mesh force - coarse-mesh force) N / kappa, FP32 [cell][8]
+template <class T>
+__global__ void k_target(const T *phic, const T *phif, int n, double scale, float *tgt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nc = (int64_t)n * n * n;
+    if (c >= nc) return;
+    const int x = (int)(c % n), y = (int)((c / n) % n), z = (int)(c / ((int64_t)n * n));
+    const int m = 2 * n;
+    auto pc = [&](int a, int b, int cc) { return (double)phic[((int64_t)wrapn(cc, n) * n + wrapn(b, n)) * n + wrapn(a, n)]; };
+    auto pf = [&](int a, int b, int cc) {
+        a = a < 0 ? a + m : (a >= m ? a - m : a);
+        b = b < 0 ? b + m : (b >= m ? b - m : b);
+        cc = cc < 0 ? cc + m : (cc >= m ? cc - m : cc);
+        return (double)phif[((int64_t)cc * m + b) * m + a];
+    };
+    const double fc[3] = {-(pc(x + 1, y, z) - pc(x - 1, y, z)) * 0.5 * n, -(pc(x, y + 1, z) - pc(x, y - 1, z)) * 0.5 * n,
+                          -(pc(x, y, z + 1) - pc(x, y, z - 1)) * 0.5 * n};
+    double ff[3] = {0, 0, 0};
+    for (int ez = -1; ez <= 1; ez++)
+        for (int ey = -1; ey <= 1; ey++)
+            for (int ex = -1; ex <= 1; ex++) {
+                const double wgt = (ex ? 0.25 : 0.5) * (ey ? 0.25 : 0.5) * (ez ? 0.25 : 0.5);
+                const int X = 2 * x + ex, Y = 2 * y + ey, Z = 2 * z + ez;
+                ff[0] -= wgt * (pf(X + 1, Y, Z) - pf(X - 1, Y, Z)) * 0.5 * m;
+                ff[1] -= wgt * (pf(X, Y + 1, Z) - pf(X, Y - 1, Z)) * 0.5 * m;
+                ff[2] -= wgt * (pf(X, Y, Z + 1) - pf(X, Y, Z - 1)) * 0.5 * m;
+            }
+    float4 *dst = reinterpret_cast<float4 *>(tgt + 8 * c);
+    dst[0] = make_float4((float)((ff[0] - fc[0]) * scale), (float)((ff[1] - fc[1]) * scale),
+                         (float)((ff[2] - fc[2]) * scale), 0.f);
+    dst[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+}  // namespace
+
+// the extra kick of a force correction c (FP32 [cell][8], channels 0..2 = force units):
+// u += dtau_kick * f * c(x_p) with f = a_n (Newtonian) or E = sqrt(a_n^2 + u^2)
+template <class T>
+__global__ void k_corr_kick(Particle<T> *part, int64_t np, const float *corr, double scale, int n, double a,
+                            double dtk, int newtonian)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    Particle<T> P = part[i];
+    const int cell = P.cell;
+    const int x = cell % n, y = (cell / n) % n, z = cell / (n * n);
+    double cv[3] = {0, 0, 0};
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++) {
+                const double w = (dx ? (double)P.f[0] : 1.0 - (double)P.f[0]) * (dy ? (double)P.f[1] : 1.0 - (double)P.f[1]) *
+                                 (dz ? (double)P.f[2] : 1.0 - (double)P.f[2]);
+                const int64_t v = ((int64_t)((z + dz) % n) * n + (y + dy) % n) * n + (x + dx) % n;
+                const float4 c4 = reinterpret_cast<const float4 *>(corr + 8 * v)[0];
+                cv[0] += w * c4.x;
+                cv[1] += w * c4.y;
+                cv[2] += w * c4.z;
+            }
+    double f = a * scale;
+    if (!newtonian) {
+        const double u0 = P.u[0], u1 = P.u[1], u2 = P.u[2];
+        f = sqrt(a * a + u0 * u0 + u1 * u1 + u2 * u2) * scale;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) P.u[k] = (T)((double)P.u[k] + dtk * f * cv[k]);
+    part[i] = P;
+}
+
+template <class T> void launch_corr_kick(Ctx &c, const StepScalars &s)
+{
+    if (!c.corr) return;
+    const int64_t nb = (c.np + 255) / 256;
+    k_corr_kick<T><<<(unsigned)nb, 256, 0, c.stream>>>(reinterpret_cast<Particle<T> *>(c.part[c.cur]), c.np,
+                                                         static_cast<const float *>(c.corr), (double)c.corr_scale,
+                                                         c.N, s.a, s.dtau_kick, s.newtonian);
+    c.launches++;
+}
+template void launch_corr_kick<float>(Ctx &, const StepScalars &);
+template void launch_corr_kick<double>(Ctx &, const StepScalars &);
+
+}  // namespace pm
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+using namespace pm;
+
+struct pm_net {
+    int n = 0;
+    int64_t ncell = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // NPARAM each
+    __nv_bfloat16 *wf = nullptr, *wt = nullptr;                            // NL * WSZ each
+    float *bias = nullptr;                                                 // NL * CH
+    __nv_bfloat16 *act[NL] = {};      // act[0] = inputs, act[l] = output of layer l-1 ([cell][16])
+    __nv_bfloat16 *g0 = nullptr, *g1 = nullptr;   // gradient ping-pong ([cell][16])
+    float *out = nullptr;             // network output [cell][8]
+    double *dloss = nullptr;
+    int64_t adam_t = 0;
+};
+
+namespace {
+
+pm_status net_fail(pm_net *e, pm_status st, const char *msg)
+{
+    e->err = msg;
+    return st;
+}
+
+unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+void conv_launch(pm_net *e, int layer, const __nv_bfloat16 *in, void *out, bool transposed, bool relu, bool f32)
+{
+    const int n = e->n, ntiles = (n / TT) * (n / TT) * (n / TT);
+    const uint4 *w = reinterpret_cast<const uint4 *>((transposed ? e->wt : e->wf) + (size_t)layer * WSZ);
+    const float *b = transposed ? nullptr : e->bias + layer * CH;
+    const uint4 *x = reinterpret_cast<const uint4 *>(in);
+    if (f32)
+        k_conv<1, false, true><<<ntiles, CONV_THREADS, 0, e->stream>>>(x, w, b, out, n);
+    else if (relu)
+        k_conv<2, true, false><<<ntiles, CONV_THREADS, 0, e->stream>>>(x, w, b, out, n);
+    else
+        k_conv<2, false, false><<<ntiles, CONV_THREADS, 0, e->stream>>>(x, w, b, out, n);
+}
+
+void net_forward(pm_net *e)
+{
+    for (int l = 0; l < NL - 1; l++) conv_launch(e, l, e->act[l], e->act[l + 1], false, true, false);
+    conv_launch(e, NL - 1, e->act[NL - 1], e->out, false, false, true);
+}
+
+int dw_blocks(int n)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (n / TT) * (n / TT) * (n / TT);
+    return std::max(1, std::min(ntiles, 2 * std::max(sms, 1)));
+}
+
+bool valid_net_n(int n) { return n >= 8 && n <= 1024 && n % 8 == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int64_t pm_net_param_count(void) { return NPARAM; }
+
+pm_status pm_net_create(int32_t n_mesh, uint64_t seed, void *stream, pm_net **out)
+{
+    if (!out) return PM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!valid_net_n(n_mesh)) return PM_ERR_UNSUPPORTED_SIZE;
+    pm_net *e = new (std::nothrow) pm_net();
+    if (!e) return PM_ERR_OOM;
+    e->n = n_mesh;
+    e->ncell = (int64_t)n_mesh * n_mesh * n_mesh;
+    e->stream = reinterpret_cast<cudaStream_t>(stream);
+    const size_t nc = (size_t)e->ncell;
+    struct A {
+        void **p;
+        size_t bytes;
+    } allocs[] = {
+        {(void **)&e->theta, sizeof(float) * NPARAM},  {(void **)&e->grad, sizeof(float) * NPARAM},
+        {(void **)&e->m, sizeof(float) * NPARAM},      {(void **)&e->v, sizeof(float) * NPARAM},
+        {(void **)&e->wf, 2 * (size_t)NL * WSZ},      {(void **)&e->wt, 2 * (size_t)NL * WSZ},
+        {(void **)&e->bias, sizeof(float) * NL * CH}, {(void **)&e->act[0], 2 * CH * nc},
+        {(void **)&e->act[1], 2 * CH * nc},            {(void **)&e->act[2], 2 * CH * nc},
+        {(void **)&e->act[3], 2 * CH * nc},            {(void **)&e->g0, 2 * CH * nc},
+        {(void **)&e->g1, 2 * CH * nc},                {(void **)&e->out, sizeof(float) * 8 * nc},
+        {(void **)&e->dloss, sizeof(double)},
+    };
+    for (const A &a : allocs)
+        if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            pm_net_destroy(e);
+            return PM_ERR_OOM;
+        }
+    // He-normal initial weights (std sqrt(2 / (27 c_in)), last layer x 0.1), zero biases and padding,
+    // from SplitMix64 + Box-Muller on the host
+    std::vector<float> th(NPARAM, 0.f);
+    uint64_t st = seed;
+    auto next = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto uni = [&]() { return ((double)(next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+    for (int l = 0; l < NL; l++) {
+        const double sd = std::sqrt(2.0 / (NOFF * CIN[l])) * (l == NL - 1 ? 0.1 : 1.0);
+        for (int d = 0; d < NOFF; d++)
+            for (int co = 0; co < COUT[l]; co++)
+                for (int ci = 0; ci < CIN[l]; ci++) {
+                    const double u1 = uni(), u2 = uni();
+                    th[(size_t)l * PSZ + (d * CH + co) * CH + ci] =
+                        (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+                }
+    }
+    pm_status s = pm_net_set_params(e, th.data());
+    if (s != PM_OK) {
+        pm_net_destroy(e);
+        return s;
+    }
+    *out = e;
+    return PM_OK;
+}
+
+void pm_net_destroy(pm_net *e)
+{
+    if (!e) return;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    else cudaDeviceSynchronize();
+    void *ps[] = {e->theta, e->grad, e->m, e->v, e->wf, e->wt, e->bias, e->act[0], e->act[1], e->act[2],
+                  e->act[3], e->g0, e->g1, e->out, e->dloss};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    cudaGetLastError();
+    delete e;
+}
+
+const char *pm_net_last_error(const pm_net *e) { return e ? e->err.c_str() : "null network"; }
+
+pm_status pm_net_set_params(pm_net *e, const float *params)
+{
+    if (!e || !params) return PM_ERR_INVALID_ARG;
+    cudaError_t ce = cudaMemcpyAsync(e->theta, params, sizeof(float) * NPARAM, cudaMemcpyDefault, e->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->grad, 0, sizeof(float) * NPARAM, e->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->m, 0, sizeof(float) * NPARAM, e->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e->v, 0, sizeof(float) * NPARAM, e->stream);
+    if (ce != cudaSuccess) return net_fail(e, PM_ERR_CUDA, "pm_net_set_params: copy failed");
+    e->adam_t = 0;
+    k_pack<<<grid_for(NPARAM, 256), 256, 0, e->stream>>>(e->theta, e->wf, e->wt, e->bias);
+    ce = cudaStreamSynchronize(e->stream);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    return ce == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_set_params: kernel failed");
+}
+
+pm_status pm_net_get_params(pm_net *e, float *params)
+{
+    if (!e || !params) return PM_ERR_INVALID_ARG;
+    cudaError_t ce = cudaMemcpyAsync(params, e->theta, sizeof(float) * NPARAM, cudaMemcpyDefault, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    return ce == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_get_params: copy failed");
+}
+
+pm_status pm_net_buffer(pm_net *e, int32_t which, void **ptr)
+{
+    if (!e || !ptr) return PM_ERR_INVALID_ARG;
+    switch (which) {
+    case PM_NET_INPUT: *ptr = e->act[0]; break;
+    case PM_NET_OUTPUT: *ptr = e->out; break;
+    case PM_NET_GRAD: *ptr = e->grad; break;
+    default: return PM_ERR_INVALID_ARG;
+    }
+    return PM_OK;
+}
+
+pm_status pm_net_forward(pm_net *e)
+{
+    if (!e) return PM_ERR_INVALID_ARG;
+    net_forward(e);
+    return cudaGetLastError() == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_forward: launch failed");
+}
+
+pm_status pm_net_backward(pm_net *e, const float *target, double *loss)
+{
+    if (!e || !target) return PM_ERR_INVALID_ARG;
+    const int64_t nc = e->ncell;
+    const int n = e->n;
+    net_forward(e);
+    cudaMemsetAsync(e->dloss, 0, sizeof(double), e->stream);
+    k_loss<<<std::min<int64_t>(grid_for(nc, CONV_THREADS), 4096), CONV_THREADS, 0, e->stream>>>(e->out, target, e->g0,
+                                                                                                  e->dloss, nc);
+    const unsigned mblocks = (unsigned)std::min<int64_t>(grid_for(nc * CH, CONV_THREADS), 4096);
+    const int dwb = dw_blocks(n);
+    __nv_bfloat16 *g = e->g0, *h = e->g1;
+    for (int l = NL - 1; l >= 0; l--) {
+        // g holds dL/d(output of layer l); mask by the ReLU and accumulate the bias gradient
+        k_mask<<<mblocks, CONV_THREADS, 0, e->stream>>>(g, l < NL - 1 ? e->act[l + 1] : g, h,
+                                                        e->grad + (size_t)l * PSZ + WSZ, nc, l < NL - 1);
+        k_conv_dw<<<dwb, CONV_THREADS, 0, e->stream>>>(reinterpret_cast<const uint4 *>(e->act[l]),
+                                                      reinterpret_cast<const uint4 *>(h), e->grad + (size_t)l * PSZ, n);
+        if (l > 0) conv_launch(e, l, h, g, true, false, false);   // dL/d(output of layer l - 1)
+    }
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess && loss) {
+        ce = cudaMemcpyAsync(loss, e->dloss, sizeof(double), cudaMemcpyDeviceToHost, e->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    }
+    return ce == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_backward: launch failed");
+}
+
+pm_status pm_net_adam(pm_net *e, float lr)
+{
+    if (!e || !(lr > 0.f)) return PM_ERR_INVALID_ARG;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    e->adam_t++;
+    const float c1 = (float)(1.0 - std::pow((double)b1, (double)e->adam_t));
+    const float c2 = (float)(1.0 - std::pow((double)b2, (double)e->adam_t));
+    k_adam<<<grid_for(NPARAM, 256), 256, 0, e->stream>>>(e->theta, e->grad, e->m, e->v, lr, b1, b2, eps, c1, c2);
+    k_pack<<<grid_for(NPARAM, 256), 256, 0, e->stream>>>(e->theta, e->wf, e->wt, e->bias);
+    return cudaGetLastError() == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_adam: launch failed");
+}
+
+pm_status pm_net_train_step(pm_net *e, const float *target, float lr, double *loss)
+{
+    pm_status s = pm_net_backward(e, target, loss);
+    if (s != PM_OK) return s;
+    return pm_net_adam(e, lr);
+}
+
+static pm_status check_solved(pm_ctx *ctx)
+{
+    if (!ctx) return PM_ERR_INVALID_ARG;
+    const Ctx &c = ctx->c;
+    if (!c.newtonian) return PM_ERR_UNSUPPORTED_SIZE;   // the correction is trained on the Newtonian force
+    if (c.stage != 2) return PM_ERR_STATE;
+    return PM_OK;
+}
+
+pm_status pm_net_features(pm_net *e, pm_ctx *ctx)
+{
+    if (!e) return PM_ERR_INVALID_ARG;
+    pm_status s = check_solved(ctx);
+    if (s != PM_OK) return net_fail(e, s, "pm_net_features: needs a solved Newtonian context");
+    Ctx &c = ctx->c;
+    if (c.N != e->n) return net_fail(e, PM_ERR_INVALID_ARG, "pm_net_features: mesh size differs");
+    const double a = c.a_n[c.step];
+    const double inv_kappa = a / (c.four_pi_g * c.cfg.omega_m);
+    const double n2 = (double)c.N * c.N;
+    const unsigned nb = grid_for(e->ncell, 256);
+    if (c.mixed)
+        k_features<float><<<nb, 256, 0, e->stream>>>(static_cast<const float *>(c.src),
+                                                     static_cast<const float *>(c.phi[c.iphi_new]), inv_kappa, n2,
+                                                     e->act[0], e->ncell);
+    else
+        k_features<double><<<nb, 256, 0, e->stream>>>(static_cast<const double *>(c.src),
+                                                      static_cast<const double *>(c.phi[c.iphi_new]), inv_kappa, n2,
+                                                      e->act[0], e->ncell);
+    return cudaGetLastError() == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_features: launch failed");
+}
+
+pm_status pm_net_target(pm_net *e, pm_ctx *coarse, pm_ctx *fine, float *target)
+{
+    if (!e || !target) return PM_ERR_INVALID_ARG;
+    pm_status s = check_solved(coarse);
+    if (s == PM_OK) s = check_solved(fine);
+    if (s != PM_OK) return net_fail(e, s, "pm_net_target: needs two solved Newtonian contexts");
+    Ctx &c = coarse->c, &f = fine->c;
+    const double a = c.a_n[c.step], af = f.a_n[f.step];
+    if (c.N != e->n || f.N != 2 * c.N || c.mixed != f.mixed || c.np != f.np || c.cfg.box_mpch != f.cfg.box_mpch ||
+        c.cfg.omega_m != f.cfg.omega_m || !(std::fabs(a - af) <= 1e-12 * a))
+        return net_fail(e, PM_ERR_INVALID_ARG, "pm_net_target: contexts do not pair (fine mesh = 2 x coarse, same a)");
+    const double scale = (double)c.N * a / (c.four_pi_g * c.cfg.omega_m);
+    const unsigned nb = grid_for(e->ncell, 128);
+    if (c.mixed)
+        k_target<float><<<nb, 128, 0, e->stream>>>(static_cast<const float *>(c.phi[c.iphi_new]),
+                                                   static_cast<const float *>(f.phi[f.iphi_new]), c.N, scale, target);
+    else
+        k_target<double><<<nb, 128, 0, e->stream>>>(static_cast<const double *>(c.phi[c.iphi_new]),
+                                                    static_cast<const double *>(f.phi[f.iphi_new]), c.N, scale, target);
+    return cudaGetLastError() == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_target: launch failed");
+}
+
+pm_status pm_net_apply(pm_net *e, pm_ctx *ctx)
+{
+    pm_status s = pm_net_features(e, ctx);
+    if (s != PM_OK) return s;
+    net_forward(e);
+    if (cudaGetLastError() != cudaSuccess) return net_fail(e, PM_ERR_CUDA, "pm_net_apply: launch failed");
+    // the kick reads the network output in force units: c = (kappa / N) y with kappa = 4piG Omega_m / a
+    Ctx &c = ctx->c;
+    const double a = c.a_n[c.step];
+    c.corr = e->out;
+    c.corr_scale = (float)(c.four_pi_g * c.cfg.omega_m / a / (double)c.N);
+    return PM_OK;
+}
+
+pm_status pm_set_correction(pm_ctx *ctx, const float *corr)
+{
+    if (!ctx) return PM_ERR_INVALID_ARG;
+    ctx->c.corr = const_cast<float *>(corr);
+    ctx->c.corr_scale = 1.f;
+    return PM_OK;
+}
+
+pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float *bias, int32_t c_out, int32_t relu,
+                            void *y, void *stream)
+{
+    if (!valid_net_n(n)) return PM_ERR_UNSUPPORTED_SIZE;
+    if (!x || !w || !y || (c_out != 8 && c_out != 16) || (c_out == 8 && relu)) return PM_ERR_INVALID_ARG;
+    const int ntiles = (n / TT) * (n / TT) * (n / TT);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint4 *xx = static_cast<const uint4 *>(x), *ww = static_cast<const uint4 *>(w);
+    if (c_out == 8)
+        k_conv<1, false, true><<<ntiles, CONV_THREADS, 0, st>>>(xx, ww, bias, y, n);
+    else if (relu)
+        k_conv<2, true, false><<<ntiles, CONV_THREADS, 0, st>>>(xx, ww, bias, y, n);
+    else
+        k_conv<2, false, false><<<ntiles, CONV_THREADS, 0, st>>>(xx, ww, bias, y, n);
+    return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+}
+
+pm_status pm_conv3d_backward_weight(int32_t n, const void *x, const void *g, float *dw, void *stream)
+{
+    if (!valid_net_n(n)) return PM_ERR_UNSUPPORTED_SIZE;
+    if (!x || !g || !dw) return PM_ERR_INVALID_ARG;
+    k_conv_dw<<<dw_blocks(n), CONV_THREADS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        static_cast<const uint4 *>(x), static_cast<const uint4 *>(g), dw, n);
+    return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+}
+
+}  // extern "C"

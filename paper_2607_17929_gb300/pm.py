@@ -73,6 +73,23 @@ def _load():
         "pm_ensemble_tune": ([vp, C.POINTER(i32)], C.c_int),
         "pm_ensemble_stream": ([vp, C.POINTER(vp)], C.c_int),
         "pm_power_spectrum_noalloc": ([vp, i64, i32, C.c_double, i32, dp, dp, C.POINTER(i64), vp], C.c_int),
+        "pm_net_param_count": ([], i64),
+        "pm_net_create": ([i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
+        "pm_net_destroy": ([vp], None),
+        "pm_net_last_error": ([vp], C.c_char_p),
+        "pm_net_set_params": ([vp, vp], C.c_int),
+        "pm_net_get_params": ([vp, vp], C.c_int),
+        "pm_net_buffer": ([vp, i32, C.POINTER(vp)], C.c_int),
+        "pm_net_features": ([vp, vp], C.c_int),
+        "pm_net_target": ([vp, vp, vp, vp], C.c_int),
+        "pm_net_forward": ([vp], C.c_int),
+        "pm_net_backward": ([vp, vp, dp], C.c_int),
+        "pm_net_adam": ([vp, C.c_float], C.c_int),
+        "pm_net_train_step": ([vp, vp, C.c_float, dp], C.c_int),
+        "pm_net_apply": ([vp, vp], C.c_int),
+        "pm_set_correction": ([vp, vp], C.c_int),
+        "pm_conv3d_forward": ([i32, vp, vp, vp, i32, i32, vp, vp], C.c_int),
+        "pm_conv3d_backward_weight": ([i32, vp, vp, vp, vp], C.c_int),
         "pm_save": ([vp, C.c_char_p], C.c_int),
         "pm_load": ([vp, C.c_char_p], C.c_int),
     }
@@ -89,7 +106,10 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_update", "pm_step", "pm_put_particles", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
             "pm_power_spectrum_noalloc", "pm_ensemble_init", "pm_ensemble_destroy", "pm_ensemble_last_error",
             "pm_ensemble_box", "pm_ensemble_set_particles", "pm_ensemble_step", "pm_ensemble_sync", "pm_ensemble_tune",
-            "pm_ensemble_stream",
+            "pm_ensemble_stream", "pm_net_param_count", "pm_net_create", "pm_net_destroy", "pm_net_last_error",
+            "pm_net_set_params", "pm_net_get_params", "pm_net_buffer", "pm_net_features", "pm_net_target",
+            "pm_net_forward", "pm_net_backward", "pm_net_adam", "pm_net_train_step", "pm_net_apply",
+            "pm_set_correction", "pm_conv3d_forward", "pm_conv3d_backward_weight",
             "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
 
 
@@ -106,6 +126,11 @@ def _ptr(a):
             raise ValueError("array must be C-contiguous")
         return a.ctypes.data
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    """Raw cudaStream_t of a torch.cuda.Stream, a raw handle, or None (default stream)."""
+    return None if stream is None else getattr(stream, "cuda_stream", stream)
 
 
 def _check(ctx, st):
@@ -282,6 +307,98 @@ def pm_ensemble_tune(e):
     k = C.c_int32()
     _echeck(e, lib.pm_ensemble_tune(e, C.byref(k)))
     return k.value
+
+
+# ---- learned force correction ---------------------------------------------------------------------
+
+PM_NET_INPUT, PM_NET_OUTPUT, PM_NET_GRAD = 0, 1, 2
+
+
+def _ncheck(net, st):
+    if st != PM_OK:
+        raise PMError(st, lib.pm_net_last_error(net).decode() if net else "")
+
+
+def pm_net_param_count():
+    return int(lib.pm_net_param_count())
+
+
+def pm_net_create(n_mesh, seed=0, stream=None):
+    h = C.c_void_p()
+    st = lib.pm_net_create(int(n_mesh), C.c_uint64(int(seed)), _stream(stream), C.byref(h))
+    if st != PM_OK:
+        raise PMError(st, "pm_net_create failed")
+    return h.value
+
+
+def pm_net_destroy(net):
+    lib.pm_net_destroy(net)
+
+
+def pm_net_last_error(net):
+    return lib.pm_net_last_error(net).decode()
+
+
+def pm_net_set_params(net, params):
+    _ncheck(net, lib.pm_net_set_params(net, _ptr(params)))
+
+
+def pm_net_get_params(net, params):
+    _ncheck(net, lib.pm_net_get_params(net, _ptr(params)))
+
+
+def pm_net_buffer(net, which):
+    h = C.c_void_p()
+    _ncheck(net, lib.pm_net_buffer(net, int(which), C.byref(h)))
+    return h.value
+
+
+def pm_net_features(net, ctx):
+    _ncheck(net, lib.pm_net_features(net, ctx))
+
+
+def pm_net_target(net, coarse, fine, target):
+    _ncheck(net, lib.pm_net_target(net, coarse, fine, _ptr(target)))
+
+
+def pm_net_forward(net):
+    _ncheck(net, lib.pm_net_forward(net))
+
+
+def pm_net_backward(net, target, want_loss=True):
+    loss = C.c_double(0.0)
+    _ncheck(net, lib.pm_net_backward(net, _ptr(target), C.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def pm_net_adam(net, lr):
+    _ncheck(net, lib.pm_net_adam(net, C.c_float(lr)))
+
+
+def pm_net_train_step(net, target, lr, want_loss=True):
+    loss = C.c_double(0.0)
+    _ncheck(net, lib.pm_net_train_step(net, _ptr(target), C.c_float(lr), C.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def pm_net_apply(net, ctx):
+    _ncheck(net, lib.pm_net_apply(net, ctx))
+
+
+def pm_set_correction(ctx, corr):
+    _check(ctx, lib.pm_set_correction(ctx, _ptr(corr)))
+
+
+def pm_conv3d_forward(n, x, w, bias, c_out, relu, y, stream=None):
+    st = lib.pm_conv3d_forward(int(n), _ptr(x), _ptr(w), _ptr(bias), int(c_out), int(relu), _ptr(y), _stream(stream))
+    if st != PM_OK:
+        raise PMError(st, "pm_conv3d_forward failed")
+
+
+def pm_conv3d_backward_weight(n, x, g, dw, stream=None):
+    st = lib.pm_conv3d_backward_weight(int(n), _ptr(x), _ptr(g), _ptr(dw), _stream(stream))
+    if st != PM_OK:
+        raise PMError(st, "pm_conv3d_backward_weight failed")
 
 
 class PM:

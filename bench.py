@@ -180,21 +180,9 @@ def make_ics(n, box, seed, a0, a_m):
 
 
 def half_step_back(a0, dtau0, box):
-    """a at tau_0 - dtau_0/2 from the library's own schedule scalars (Newton on the conformal-time integral)."""
-    h0 = box / 2997.92458
-    def hc(a):
-        return a * h0 * math.sqrt(OM / a ** 3 + 1 - OM)
-    # Gauss-Legendre 16 points is ample for half a step
-    import numpy as np
-    x, w = np.polynomial.legendre.leggauss(16)
-    def tau(a_lo, a_hi):
-        m, r = 0.5 * (a_lo + a_hi), 0.5 * (a_hi - a_lo)
-        return r * sum(wi / ((m + r * xi) * hc(m + r * xi)) for xi, wi in zip(x, w))
-    a = a0 * math.exp(-0.5 * dtau0 * hc(a0))
-    for _ in range(50):
-        g = tau(a, a0) - 0.5 * dtau0
-        a += g * a * hc(a)
-    return a
+    """a at tau_0 - dtau_0/2 from the library's own schedule scalars."""
+    from paper_2607_17929_gb300 import ics
+    return ics.a_half_step_before(a0, dtau0, OM, box)
 
 
 ENSEMBLE_SIDES = (64,) * 16 + (128,) * 16 + (192,) * 16
@@ -289,6 +277,66 @@ def ensemble_bench(pm, torch, steps, warmup):
             "ic_seconds": round(t_ic, 1)}
 
 
+def correction_bench(pm, torch, reps=20):
+    """Learned force correction at its 256^3 workload (500 Mpc/h, Newtonian): network forward (4 conv layers on
+    the tensor cores), one training step, and the plain vs corrected step, all timed with CUDA events."""
+    n, box = 256, 500.0
+    probe = pm.PM(8, 8, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED, pm.PM_NEWTONIAN)
+    a_n, dtau, _ = probe.schedule()
+    probe.close()
+    pos, mom = make_ics(n, box, 1234, a_n[0], half_step_back(a_n[0], dtau[0], box))
+    sim = pm.PM(n, n ** 3, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED, pm.PM_NEWTONIAN)
+    sim.set_particles(torch.from_numpy(pos).cuda(), torch.from_numpy(mom).cuda())
+    net = pm.pm_net_create(n, 1)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / k
+
+    plain_ms = timed(sim.step, reps)
+
+    def corrected():
+        sim.project()
+        sim.solve()
+        pm.pm_net_apply(net, sim.ctx)
+        sim.update()
+    corr_ms = timed(corrected, reps)
+    fwd_ms = timed(lambda: pm.pm_net_forward(net), reps)
+    tgt = torch.zeros((n ** 3, 8), dtype=torch.float32, device="cuda")
+    train_ms = timed(lambda: pm.pm_net_backward(net, tgt, want_loss=False), 5)
+    sim.close()
+    pm.pm_net_destroy(net)
+    cells = n ** 3
+    padded = 2 * 27 * 16 * cells * (16 * 3 + 8)          # the kernels' MMA work (channels padded to 16 / 8)
+    useful = 2 * 27 * cells * (2 * 16 + 16 * 16 + 16 * 16 + 16 * 3)
+    peak = load_bf16_peak()
+    return {"workload": "256^3 mesh and particles, 500 Mpc/h, Newtonian, mixed; network 2-16-16-16-3, 3^3 conv, "
+                        "BF16/FP32, He-initialised weights (timing does not depend on them)",
+            "plain_step_ms": round(plain_ms, 3), "corrected_step_ms": round(corr_ms, 3),
+            "forward_ms": round(fwd_ms, 3), "forward_backward_ms": round(train_ms, 3),
+            "roofline": {"bound": "tensor", "kernel": "k_conv (4 layers)", "achieved": round(padded / (fwd_ms * 1e-3) / 1e12, 1),
+                         "peak": peak, "unit": "TFLOP/s", "frac": round(padded / (fwd_ms * 1e-3) / 1e12 / peak, 4),
+                         "flops_padded": padded, "flops_useful": useful,
+                         "note": "mma.sync m16n8k16 BF16 (legacy tensor path); of measured bf16 burst peak"}}
+
+
+def load_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def cpu_oracle_rate(n, steps, box):
     """Particle updates per second of the FP64 C oracle (single thread) on an n^3 sample."""
     from oracle import oracle as O
@@ -350,6 +398,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-correction", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=10)
     args = ap.parse_args()
@@ -472,6 +521,11 @@ def main():
                               "kernels_ms": {k: round(v, 4) for k, v in kernv.items()}}
         torch.cuda.empty_cache()
 
+    correction = None
+    if not args.no_correction:
+        correction = correction_bench(pm, torch)
+        torch.cuda.empty_cache()
+
     ensemble = None
     if not args.no_ensemble:
         ensemble = ensemble_bench(pm, torch, args.ensemble_steps, 3)
@@ -523,6 +577,7 @@ def main():
             "fp64": fp64,
             "variants": variants,
             "ensemble": ensemble,
+            "correction": correction,
             "e2e": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                     "how": "pm_put_particles(pinned host f64 pos, mom) + pm_step + pm_get_particles(pinned host)"},

@@ -317,6 +317,9 @@ pm_status pm_net_get_params(pm_net *net, float *params);
  * pm_net_adam).  Owned by the network. */
 pm_status pm_net_buffer(pm_net *net, int32_t which, void **ptr);
 
+/* Normalisation (default 1, 1, 1): the inputs become s_delta x0 and s_phi x1,
+ * the targets s_target y*, and the applied correction (kappa / N) y / s_target. */
+pm_status pm_net_set_scales(pm_net *net, double s_delta, double s_phi, double s_target);
 /* Inputs x0, x1 from a context after pm_solve (Newtonian mode, same n_mesh). */
 pm_status pm_net_features(pm_net *net, pm_ctx *ctx);
 /* Training target (FP32 [cell][8], device) from a solved context and a

@@ -304,14 +304,14 @@ __global__ void k_adam(float *theta, float *grad, float *m, float *v, float lr, 
     grad[i] = 0.f;
 }
 
-// network inputs from a solved context: channel 0 = delta = R / kappa, channel 1 = phi N^2 / kappa
+// network inputs from a solved context: channel 0 = s_delta R / kappa, channel 1 = s_phi phi N^2 / kappa
 template <class T>
-__global__ void k_features(const T *R, const T *phi, double inv_kappa, double n2, __nv_bfloat16 *x, int64_t ncell)
+__global__ void k_features(const T *R, const T *phi, double s0, double s1, __nv_bfloat16 *x, int64_t ncell)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     __nv_bfloat162 v[8];
-    v[0] = __floats2bfloat162_rn((float)((double)R[c] * inv_kappa), (float)((double)phi[c] * n2 * inv_kappa));
+    v[0] = __floats2bfloat162_rn((float)((double)R[c] * s0), (float)((double)phi[c] * s1));
 #pragma unroll
     for (int k = 1; k < 8; k++) v[k] = __floats2bfloat162_rn(0.f, 0.f);
     uint4 *dst = reinterpret_cast<uint4 *>(x + 16 * c);
@@ -423,6 +423,7 @@ struct pm_net {
     float *out = nullptr;             // network output [cell][8]
     double *dloss = nullptr;
     int64_t adam_t = 0;
+    double s_delta = 1.0, s_phi = 1.0, s_target = 1.0;   // input and target normalisation
 };
 
 namespace {
@@ -654,15 +655,15 @@ pm_status pm_net_features(pm_net *e, pm_ctx *ctx)
     if (c.N != e->n) return net_fail(e, PM_ERR_INVALID_ARG, "pm_net_features: mesh size differs");
     const double a = c.a_n[c.step];
     const double inv_kappa = a / (c.four_pi_g * c.cfg.omega_m);
-    const double n2 = (double)c.N * c.N;
+    const double s0 = e->s_delta * inv_kappa, s1 = e->s_phi * (double)c.N * c.N * inv_kappa;
     const unsigned nb = grid_for(e->ncell, 256);
     if (c.mixed)
         k_features<float><<<nb, 256, 0, e->stream>>>(static_cast<const float *>(c.src),
-                                                     static_cast<const float *>(c.phi[c.iphi_new]), inv_kappa, n2,
+                                                     static_cast<const float *>(c.phi[c.iphi_new]), s0, s1,
                                                      e->act[0], e->ncell);
     else
         k_features<double><<<nb, 256, 0, e->stream>>>(static_cast<const double *>(c.src),
-                                                      static_cast<const double *>(c.phi[c.iphi_new]), inv_kappa, n2,
+                                                      static_cast<const double *>(c.phi[c.iphi_new]), s0, s1,
                                                       e->act[0], e->ncell);
     return cudaGetLastError() == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_features: launch failed");
 }
@@ -678,7 +679,7 @@ pm_status pm_net_target(pm_net *e, pm_ctx *coarse, pm_ctx *fine, float *target)
     if (c.N != e->n || f.N != 2 * c.N || c.mixed != f.mixed || c.np != f.np || c.cfg.box_mpch != f.cfg.box_mpch ||
         c.cfg.omega_m != f.cfg.omega_m || !(std::fabs(a - af) <= 1e-12 * a))
         return net_fail(e, PM_ERR_INVALID_ARG, "pm_net_target: contexts do not pair (fine mesh = 2 x coarse, same a)");
-    const double scale = (double)c.N * a / (c.four_pi_g * c.cfg.omega_m);
+    const double scale = e->s_target * (double)c.N * a / (c.four_pi_g * c.cfg.omega_m);
     const unsigned nb = grid_for(e->ncell, 128);
     if (c.mixed)
         k_target<float><<<nb, 128, 0, e->stream>>>(static_cast<const float *>(c.phi[c.iphi_new]),
@@ -695,11 +696,22 @@ pm_status pm_net_apply(pm_net *e, pm_ctx *ctx)
     if (s != PM_OK) return s;
     net_forward(e);
     if (cudaGetLastError() != cudaSuccess) return net_fail(e, PM_ERR_CUDA, "pm_net_apply: launch failed");
-    // the kick reads the network output in force units: c = (kappa / N) y with kappa = 4piG Omega_m / a
+    // the kick reads the network output in force units: c = (kappa / N) y / s_target, kappa = 4piG Omega_m / a
     Ctx &c = ctx->c;
     const double a = c.a_n[c.step];
     c.corr = e->out;
-    c.corr_scale = (float)(c.four_pi_g * c.cfg.omega_m / a / (double)c.N);
+    c.corr_scale = (float)(c.four_pi_g * c.cfg.omega_m / a / (double)c.N / e->s_target);
+    return PM_OK;
+}
+
+pm_status pm_net_set_scales(pm_net *e, double s_delta, double s_phi, double s_target)
+{
+    if (!e || !(s_delta > 0) || !(s_phi >= 0) || !(s_target > 0) || !std::isfinite(s_delta) || !std::isfinite(s_phi) ||
+        !std::isfinite(s_target))
+        return PM_ERR_INVALID_ARG;
+    e->s_delta = s_delta;
+    e->s_phi = s_phi;
+    e->s_target = s_target;
     return PM_OK;
 }
 

@@ -179,3 +179,26 @@ def plane_wave_ics(n_side: int, amplitude: float, mode: int, a_pos: float,
     pos = pos - np.floor(pos)
     mom = (a_vel * hc_v * fv * dv / dp) * psi
     return np.ascontiguousarray(pos), np.ascontiguousarray(mom)
+
+
+def a_half_step_before(a0: float, dtau0: float, omega_m: float, box_mpch: float) -> float:
+    """Scale factor at tau_0 - dtau_0 / 2, where the initial momenta live (leap-frog staggering): Newton's
+    method on the conformal-time integral int da / (a Hc), Hc = a H0 sqrt(Omega_m / a^3 + 1 - Omega_m),
+    with 16-point Gauss-Legendre quadrature over the half step."""
+    h0 = box_mpch / 2997.92458
+
+    def hc(a):
+        return a * h0 * math.sqrt(omega_m / a ** 3 + 1 - omega_m)
+
+    x, w = np.polynomial.legendre.leggauss(16)
+
+    def tau(a_lo, a_hi):
+        m, r = 0.5 * (a_lo + a_hi), 0.5 * (a_hi - a_lo)
+        return r * sum(wi / ((m + r * xi) * hc(m + r * xi)) for xi, wi in zip(x, w))
+
+    a = a0 * math.exp(-0.5 * dtau0 * hc(a0))
+    for _ in range(50):
+        g = tau(a, a0) - 0.5 * dtau0
+        a += g * a * hc(a)
+    return a
+

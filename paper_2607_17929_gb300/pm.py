@@ -88,6 +88,7 @@ def _load():
         "pm_net_train_step": ([vp, vp, C.c_float, dp], C.c_int),
         "pm_net_apply": ([vp, vp], C.c_int),
         "pm_set_correction": ([vp, vp], C.c_int),
+        "pm_net_set_scales": ([vp, C.c_double, C.c_double, C.c_double], C.c_int),
         "pm_conv3d_forward": ([i32, vp, vp, vp, i32, i32, vp, vp], C.c_int),
         "pm_conv3d_backward_weight": ([i32, vp, vp, vp, vp], C.c_int),
         "pm_save": ([vp, C.c_char_p], C.c_int),
@@ -109,7 +110,7 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_ensemble_stream", "pm_net_param_count", "pm_net_create", "pm_net_destroy", "pm_net_last_error",
             "pm_net_set_params", "pm_net_get_params", "pm_net_buffer", "pm_net_features", "pm_net_target",
             "pm_net_forward", "pm_net_backward", "pm_net_adam", "pm_net_train_step", "pm_net_apply",
-            "pm_set_correction", "pm_conv3d_forward", "pm_conv3d_backward_weight",
+            "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight",
             "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
 
 
@@ -383,6 +384,10 @@ def pm_net_train_step(net, target, lr, want_loss=True):
 
 def pm_net_apply(net, ctx):
     _ncheck(net, lib.pm_net_apply(net, ctx))
+
+
+def pm_net_set_scales(net, s_delta, s_phi, s_target):
+    _ncheck(net, lib.pm_net_set_scales(net, float(s_delta), float(s_phi), float(s_target)))
 
 
 def pm_set_correction(ctx, corr):

@@ -295,3 +295,21 @@ def test_zero_network_leaves_the_step_unchanged(env):
     assert np.sqrt(np.mean(((p1 - p2 + 0.5) % 1.0 - 0.5) ** 2)) * n < 1e-6 and rel(u2, u1) < 1e-5
     pm.pm_net_destroy(net)
     g1.close(); g2.close()
+
+
+def test_training_driver_end_to_end_small(env):
+    """The training and evaluation loops at 16^3 (one seed, two snapshots, a few iterations)."""
+    torch, pm = env
+    from paper_2607_17929_gb300 import correction as CR
+    n, box = 16, 500.0 * 16 / 256
+    net = pm.pm_net_create(n, 1)
+    pairs = CR.make_pairs(pm, torch, net, [7], {60, 99}, n, box, log=lambda *_: None)
+    assert len(pairs) == 2 and all(torch.isfinite(t).all() for _, t, _, _ in pairs)
+    losses = CR.train(pm, torch, net, pairs, 20, log=lambda *_: None)
+    assert all(np.isfinite(losses))
+    ev = CR.explained_variance(pm, torch, net, pairs)
+    assert all(np.isfinite(e["mse"]) for e in ev)
+    res = CR.evaluate(pm, torch, net, 9, n, box, log=lambda *_: None)
+    for name in ("plain", "corrected"):
+        assert np.isfinite(res[name]["rms_displacement_error_cells"])
+    pm.pm_net_destroy(net)

@@ -356,38 +356,40 @@ __global__ void k_target(const T *phic, const T *phif, int n, double scale, floa
 }  // namespace
 
 // the extra kick of a force correction c (FP32 [cell][8], channels 0..2 = force units):
-// u += dtau_kick * f * c(x_p) with f = a_n (Newtonian) or E = sqrt(a_n^2 + u^2)
+// u += dtau_kick * f * c(x_p) with f = a_n (Newtonian) or E = sqrt(a_n^2 + u^2), in the
+// context's precision (FP32 in the mixed form: FP64 arithmetic is slow on this part)
 template <class T>
-__global__ void k_corr_kick(Particle<T> *part, int64_t np, const float *corr, double scale, int n, double a,
-                            double dtk, int newtonian)
+__global__ void k_corr_kick(Particle<T> *part, int64_t np, const float *corr, T scale, int n, T a, T dtk,
+                            int newtonian)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     Particle<T> P = part[i];
     const int cell = P.cell;
     const int x = cell % n, y = (cell / n) % n, z = cell / (n * n);
-    double cv[3] = {0, 0, 0};
+    const int xp = x + 1 == n ? 0 : x + 1, yp = y + 1 == n ? 0 : y + 1, zp = z + 1 == n ? 0 : z + 1;
+    const T wx[2] = {T(1) - P.f[0], P.f[0]}, wy[2] = {T(1) - P.f[1], P.f[1]}, wz[2] = {T(1) - P.f[2], P.f[2]};
+    const int xs[2] = {x, xp}, ys[2] = {y, yp}, zs[2] = {z, zp};
+    T cv[3] = {0, 0, 0};
 #pragma unroll
     for (int dz = 0; dz < 2; dz++)
 #pragma unroll
-        for (int dy = 0; dy < 2; dy++)
+        for (int dy = 0; dy < 2; dy++) {
+            const T wyz = wy[dy] * wz[dz];
+            const int64_t row = ((int64_t)zs[dz] * n + ys[dy]) * n;
 #pragma unroll
             for (int dx = 0; dx < 2; dx++) {
-                const double w = (dx ? (double)P.f[0] : 1.0 - (double)P.f[0]) * (dy ? (double)P.f[1] : 1.0 - (double)P.f[1]) *
-                                 (dz ? (double)P.f[2] : 1.0 - (double)P.f[2]);
-                const int64_t v = ((int64_t)((z + dz) % n) * n + (y + dy) % n) * n + (x + dx) % n;
-                const float4 c4 = reinterpret_cast<const float4 *>(corr + 8 * v)[0];
-                cv[0] += w * c4.x;
-                cv[1] += w * c4.y;
-                cv[2] += w * c4.z;
+                const T w = wx[dx] * wyz;
+                const float4 c4 = reinterpret_cast<const float4 *>(corr)[2 * (row + xs[dx])];
+                cv[0] += w * (T)c4.x;
+                cv[1] += w * (T)c4.y;
+                cv[2] += w * (T)c4.z;
             }
-    double f = a * scale;
-    if (!newtonian) {
-        const double u0 = P.u[0], u1 = P.u[1], u2 = P.u[2];
-        f = sqrt(a * a + u0 * u0 + u1 * u1 + u2 * u2) * scale;
-    }
+        }
+    T f = a * scale;
+    if (!newtonian) f = sqrt(a * a + P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]) * scale;
 #pragma unroll
-    for (int k = 0; k < 3; k++) P.u[k] = (T)((double)P.u[k] + dtk * f * cv[k]);
+    for (int k = 0; k < 3; k++) P.u[k] += dtk * f * cv[k];
     part[i] = P;
 }
 
@@ -396,8 +398,8 @@ template <class T> void launch_corr_kick(Ctx &c, const StepScalars &s)
     if (!c.corr) return;
     const int64_t nb = (c.np + 255) / 256;
     k_corr_kick<T><<<(unsigned)nb, 256, 0, c.stream>>>(reinterpret_cast<Particle<T> *>(c.part[c.cur]), c.np,
-                                                         static_cast<const float *>(c.corr), (double)c.corr_scale,
-                                                         c.N, s.a, s.dtau_kick, s.newtonian);
+                                                         static_cast<const float *>(c.corr), (T)c.corr_scale, c.N,
+                                                         (T)s.a, (T)s.dtau_kick, s.newtonian);
     c.launches++;
 }
 template void launch_corr_kick<float>(Ctx &, const StepScalars &);

@@ -50,6 +50,13 @@ template <> struct Acc<float> {
     __device__ __forceinline__ float lo() const { return c; }
 };
 
+// 1 / sqrt(x) and a / b: the hardware approximations (a few ulp) in the mixed form, whose
+// FP32 rounding already sets the error; IEEE operations in FP64
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
+
 template <class T> __device__ __forceinline__ T mulr(T a, T b);
 template <> __device__ __forceinline__ float mulr<float>(float a, float b) { return __fmul_rn(a, b); }
 template <> __device__ __forceinline__ double mulr<double>(double a, double b) { return __dmul_rn(a, b); }
@@ -130,7 +137,7 @@ template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 1024;
 
 template <class T> size_t dep_smem()
 {
-    return sizeof(T) * (12 * dep_cap<T>() + 2 * NFLD) + sizeof(double) * 32 +
+    return sizeof(T) * (12 * dep_cap<T>() + 2 * NFLD) +
            sizeof(int) * (3 * NREG + 64 + FLD * FLD + FLD);
 }
 
@@ -140,8 +147,6 @@ template <class T> struct alignas(16) DepRec {
     T f[3], q00, q0[3], txx, txy, txz, tyy, tyz;
 };
 static_assert(sizeof(DepRec<float>) == 48 && sizeof(DepRec<double>) == 96, "packed record");
-// 2 * NFLD field values keep the following f64 scratch 8-byte aligned
-static_assert((sizeof(float) * 2 * NFLD) % 8 == 0, "alignment");
 
 // Exclusive scan of v[0..n) (n <= 2 * blockDim) in place; returns the total.
 __device__ int block_exclusive_scan(int *v, int n, int *warp_tmp)
@@ -185,8 +190,7 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
     DepRec<T> *rec = reinterpret_cast<DepRec<T> *>(smem);            // [CAP]
     T *sphi = reinterpret_cast<T *>(rec + CAP);
     T *schi = sphi + NFLD;
-    double *sred = reinterpret_cast<double *>(schi + NFLD);          // 32 doubles
-    int *scnt = reinterpret_cast<int *>(sred + 32);
+    int *scnt = reinterpret_cast<int *>(schi + NFLD);
     int *soff = scnt + NREG;
     int *sgs = soff + NREG;
     int *wtmp = sgs + NREG;                                          // 64 ints
@@ -234,7 +238,8 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
     Acc<T> acc00;
     acc00.zero();
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double k0 = 0.0;
+    Acc<T> k0;   // this thread's share of the k = 0 excess (float-float in the mixed form)
+    k0.zero();
     const bool full = p.full;
 
     for (int lo = 0; lo < total; lo += CAP) {
@@ -275,13 +280,17 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
                 }
                 const T ux = P.u[0], uy = P.u[1], uz = P.u[2];
                 const T u2 = ux * ux + uy * uy + uz * uz;
-                const T E = sqrt(p.a2 + u2);
-                const T iE = T(1) / E;
+                const T e2 = p.a2 + u2;
+                const T iE = rsqrt_t(e2);
+                // E = a + u^2 / (E + a): the approximate E enters only the small term, so E keeps the
+                // accuracy of a (the T^00 charge cancels against the background in R)
+                const T dE = div_t(u2, e2 * iE + p.a);
+                const T E = p.a + dE;
                 const T v2 = u2 * iE * iE;
                 const T m = p.mass;
-                // T^00 charge and its excess over a particle at rest (k = 0 mode in FP64)
+                // T^00 charge and its excess over a particle at rest (k = 0 mode, summed in FP64)
                 r.q00 = m * E * (T(1) + T(3) * ph + ph * v2);
-                if (sx >= 1 && sy >= 1 && sz >= 1) k0 += (double)(m * (u2 / (E + p.a) + E * (T(3) * ph + ph * v2)));
+                if (sx >= 1 && sy >= 1 && sz >= 1) k0.add(m * (dE + E * (T(3) * ph + ph * v2)));
                 if (full) {
                     const T wv = m * (T(1) + T(4) * ph - ch);
                     r.q0[0] = wv * ux;
@@ -335,22 +344,21 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
     T nl = T(0);
     if (p.full_hc) {
         nl = hc_remainder<T>(sphi, schi, vo, st, p.phi2[go], p);
-        k0 -= (double)nl * p.inv_g;   // the k = 0 mode carries the mean of -Nl
+        k0.add(-nl * (T)p.inv_g);   // the k = 0 mode carries the mean of -Nl
     }
 
-    // k = 0 excess: block reduction in FP64, one atomic per CTA into a slot
+    // k = 0 excess: warp reduction of the (hi, lo) pairs with TwoSum, one FP64 atomic per warp into a slot
     {
-        double v = k0;
+        T hi = k0.hi(), lo = k0.lo();
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) sred[tid >> 5] = v;
-        __syncthreads();
-        if (tid < 32) {
-            v = tid < (DEP_THREADS >> 5) ? sred[tid] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (tid == 0 && !p.newtonian) atomicAdd(&p.k0slots[b & (NK0SLOTS - 1)], v);
+        for (int o = 16; o > 0; o >>= 1) {
+            const T h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+            const T t = hi + h2, bp = t - hi;
+            lo += l2 + ((hi - (t - bp)) + (h2 - bp));
+            hi = t;
         }
+        if ((tid & 31) == 0 && !p.newtonian)
+            atomicAdd(&p.k0slots[(b * (DEP_THREADS >> 5) + (tid >> 5)) & (NK0SLOTS - 1)], (double)hi + (double)lo);
     }
 
     // epilogue: assemble the field-equation sources at vertex o
@@ -568,8 +576,10 @@ __global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_dri
             for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * u[d] * p.inv_a_half;
         } else {
             const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            const T E = sqrt(p.a2 + u2);
-            const T u2E = u2 / E;
+            const T e2 = p.a2 + u2;
+            const T iE = rsqrt_t(e2);
+            const T E = e2 * iE;
+            const T u2E = u2 * iE;
             T K[3];
 #pragma unroll
             for (int d = 0; d < 3; d++) {
@@ -579,8 +589,7 @@ __global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_dri
 #pragma unroll
             for (int d = 0; d < 3; d++) u[d] += p.dt_kick * K[d];
             const T v2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            const T Ed = sqrt(p.a_half2 + v2);
-            const T iEd = T(1) / Ed;
+            const T iEd = rsqrt_t(p.a_half2 + v2);
             const T fac = (T(1) + T(3) * val[0] - val[1] - val[0] * v2 * iEd * iEd) * iEd;
 #pragma unroll
             for (int d = 0; d < 3; d++) dx[d] = p.dt_drift_N * (u[d] * fac + val[2 + d]);

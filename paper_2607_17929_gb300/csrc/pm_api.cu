@@ -115,6 +115,21 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// An address the kernels can use for p: p itself for device memory, the mapped device address for
+// pinned host memory (page-locked by cudaHostAlloc or cudaHostRegister: the kernels then read or
+// write it across the CPU-GPU link, with no staging copy), NULL for pageable host memory.
+template <class P> P *kernel_ptr(P *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<P *>(a.devicePointer);
+    return nullptr;
+}
+
 StepScalars scalars(const Ctx &c, int k, bool bootstrap)
 {
     const Background bg(c.cfg.omega_m, c.h0);
@@ -232,13 +247,12 @@ template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const do
         c.stage = 0;
     }
     CK(cudaMemsetAsync(c.count, 0, sizeof(int32_t) * c.nc, c.stream));
-    const bool dev = is_device_ptr(pos) && is_device_ptr(mom);
+    const double *kpos = kernel_ptr(pos), *kmom = kernel_ptr(mom);
     int *dflag = reinterpret_cast<int *>(c.dscal + 4);
     CK(cudaMemsetAsync(dflag, 0, sizeof(int), c.stream));
-    if (dev) {
-        launch_check_finite<T>(c, pos, 3 * c.np, dflag);
-        launch_check_finite<T>(c, mom, 3 * c.np, dflag);
-        launch_load_particles<T>(c, pos, mom, 0, c.np);
+    if (kpos && kmom) {
+        // device or pinned host arrays: one pass reads them, checks them and builds the records
+        launch_load_particles<T>(c, kpos, kmom, 0, c.np, dflag);
         CKL("load");
     } else {
         double *st = reinterpret_cast<double *>(c.stage_buf);
@@ -248,9 +262,7 @@ template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const do
             CK(cudaMemcpyAsync(st, pos + 3 * f, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
             CK(cudaMemcpyAsync(st + 3 * chunk, mom + 3 * f, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
                                c.stream));
-            launch_check_finite<T>(c, st, 3 * n, dflag);
-            launch_check_finite<T>(c, st + 3 * chunk, 3 * n, dflag);
-            launch_load_particles<T>(c, st, st + 3 * chunk, f, n);
+            launch_load_particles<T>(c, st, st + 3 * chunk, f, n, dflag);
             CKL("load");
         }
     }
@@ -291,10 +303,12 @@ template <class T> pm_status get_particles_t(Ctx &c, double *pos, double *mom)
 {
     launch_store_particles_scatter<T>(c, pos, mom);
     CKL("unpermute");
-    const bool dev = (!pos || is_device_ptr(pos)) && (!mom || is_device_ptr(mom));
-    if (dev) {
-        launch_store_particles<T>(c, pos, mom, 0, c.np);
+    double *kpos = pos ? kernel_ptr(pos) : nullptr, *kmom = mom ? kernel_ptr(mom) : nullptr;
+    if ((!pos || kpos) && (!mom || kmom)) {
+        // device or pinned host arrays: the kernel writes them directly
+        launch_store_particles<T>(c, kpos, kmom, 0, c.np);
         CKL("store");
+        if (!is_device_ptr(pos ? (const void *)pos : (const void *)mom)) CK(cudaStreamSynchronize(c.stream));
         return PM_OK;
     }
     double *st = reinterpret_cast<double *>(c.stage_buf);

@@ -165,7 +165,8 @@ void launch_sort(Ctx &c);
 template <class T>
 void launch_corr_kick(Ctx &c, const StepScalars &s);
 template <class T>
-void launch_load_particles(Ctx &c, const double *d_pos, const double *d_mom, int64_t first, int64_t count);
+void launch_load_particles(Ctx &c, const double *d_pos, const double *d_mom, int64_t first, int64_t count,
+                           int *d_nonfinite);
 template <class T>
 void launch_store_particles(Ctx &c, double *d_pos, double *d_mom, int64_t first, int64_t count);
 template <class T>

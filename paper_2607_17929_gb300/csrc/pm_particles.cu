@@ -722,15 +722,19 @@ __global__ void __launch_bounds__(256) k_scatter(const Particle<T> *in, Particle
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_load(const double *pos, const double *mom, int64_t first, int64_t cnt, int N,
-                       Particle<T> *out, int32_t *count)
+                       Particle<T> *out, int32_t *count, int *nonfinite)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cnt) return;
     Particle<T> P{};
     int ic[3];
+    bool bad = false;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         double x = pos[3 * k + d];
+        const double u = mom[3 * k + d];
+        bad |= !isfinite(x) || !isfinite(u);
+        if (!isfinite(x)) x = 0.0;   // keeps the cell index valid; the caller rejects the input
         x -= floor(x);
         if (x >= 1.0) x = 0.0;
         double s = x * N;
@@ -744,8 +748,9 @@ __global__ void k_load(const double *pos, const double *mom, int64_t first, int6
             P.f[d] = T(0);
             ic[d] = (c + 1) % N;
         }
-        P.u[d] = (T)mom[3 * k + d];
+        P.u[d] = (T)u;
     }
+    if (bad) *nonfinite = 1;
     P.cell = (ic[2] * N + ic[1]) * N + ic[0];
     P.id = (uint32_t)(first + k);
     out[first + k] = P;
@@ -761,17 +766,40 @@ __global__ void k_unpermute(const Particle<T> *in, Particle<T> *out, int64_t np)
     out[P.id] = P;
 }
 
+// Particle records (in id order) -> f64 positions and momenta [k][3].  A block stages 512
+// particles in shared memory and writes them with 16-byte stores at consecutive addresses, which
+// keeps the writes full-line even when the destination is pinned host memory across the link.
+constexpr int ST_P = 512;
 template <class T>
-__global__ void k_store(const Particle<T> *byid, int64_t first, int64_t cnt, int N, double *pos, double *mom)
+__global__ void __launch_bounds__(256) k_store(const Particle<T> *byid, int64_t first, int64_t cnt, int N,
+                                               double inv_n, double *pos, double *mom, int vec)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= cnt) return;
-    const Particle<T> P = byid[first + k];
-    const int ic[3] = {P.cell % N, (P.cell / N) % N, P.cell / (N * N)};
+    __shared__ double sp[3 * ST_P], su[3 * ST_P];
+    const int64_t base = (int64_t)blockIdx.x * ST_P;
+    const int nb = (int)min((int64_t)ST_P, cnt - base);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const Particle<T> P = byid[first + base + j];
+        const int ic[3] = {P.cell % N, (P.cell / N) % N, P.cell / (N * N)};
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        if (pos) pos[3 * k + d] = ((double)ic[d] + (double)P.f[d]) / (double)N;
-        if (mom) mom[3 * k + d] = (double)P.u[d];
+        for (int d = 0; d < 3; d++) {
+            sp[3 * j + d] = ((double)ic[d] + (double)P.f[d]) * inv_n;
+            su[3 * j + d] = (double)P.u[d];
+        }
+    }
+    __syncthreads();
+    const int nv = 3 * nb;
+    double *dst[2] = {pos ? pos + 3 * base : nullptr, mom ? mom + 3 * base : nullptr};
+    const double *src[2] = {sp, su};
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        if (!dst[a]) continue;
+        if (vec) {
+            double2 *o = reinterpret_cast<double2 *>(dst[a]);
+            for (int v = threadIdx.x; v < nv / 2; v += blockDim.x) o[v] = make_double2(src[a][2 * v], src[a][2 * v + 1]);
+            if ((nv & 1) && threadIdx.x == 0) dst[a][nv - 1] = src[a][nv - 1];
+        } else {
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) dst[a][v] = src[a][v];
+        }
     }
 }
 
@@ -933,10 +961,12 @@ void launch_sort(Ctx &c)
 }
 
 template <class T>
-void launch_load_particles(Ctx &c, const double *d_pos, const double *d_mom, int64_t first, int64_t count)
+void launch_load_particles(Ctx &c, const double *d_pos, const double *d_mom, int64_t first, int64_t count,
+                           int *d_nonfinite)
 {
     k_load<T><<<nblk(count, 256), 256, 0, c.stream>>>(d_pos, d_mom, first, count, c.N,
-                                                      reinterpret_cast<Particle<T> *>(c.part[c.cur]), c.count);
+                                                      reinterpret_cast<Particle<T> *>(c.part[c.cur]), c.count,
+                                                      d_nonfinite);
 }
 
 template <class T>
@@ -951,8 +981,10 @@ template <class T>
 void launch_store_particles(Ctx &c, double *d_pos, double *d_mom, int64_t first, int64_t count)
 {
     const int o = 1 - c.cur;
-    k_store<T><<<nblk(count, 256), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[o]), first,
-                                                       count, c.N, d_pos, d_mom);
+    // 16-byte stores need 16-byte aligned arrays (the block offsets are multiples of 3 * 512 doubles)
+    const int vec = ((reinterpret_cast<uintptr_t>(d_pos) | reinterpret_cast<uintptr_t>(d_mom)) & 15) == 0;
+    k_store<T><<<nblk(count, ST_P), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[o]), first,
+                                                        count, c.N, 1.0 / (double)c.N, d_pos, d_mom, vec);
 }
 
 template <class T>
@@ -989,7 +1021,7 @@ void launch_check_finite(Ctx &c, const double *d, int64_t n, int *d_flag)
     template void launch_kick_drift<T>(Ctx &, const StepScalars &);                         \
     template void launch_sort<T>(Ctx &);                                                    \
     template void launch_load_particles<T>(Ctx &, const double *, const double *, int64_t,  \
-                                           int64_t);                                        \
+                                           int64_t, int *);                                 \
     template void launch_store_particles<T>(Ctx &, double *, double *, int64_t, int64_t);   \
     template void launch_store_particles_scatter<T>(Ctx &, double *, double *);             \
     template void launch_density<T>(Ctx &, void *);                                         \

@@ -148,6 +148,72 @@ __global__ void __launch_bounds__(CONV_THREADS, 3)
         }
 }
 
+// First layer (2 input channels): the K dimension packs 8 offsets x 2 channels per k16 step, so 27
+// offsets take 4 steps instead of 27 (slots of offsets 27..31 carry zero weights).  A fragments
+// are built from 4-byte (2-channel) shared-memory loads, B fragments once per thread from the
+// weights in global memory.  y = relu(conv(x, w) + b), BF16 [cell][16].
+__global__ void __launch_bounds__(CONV_THREADS, 3)
+    k_conv_in2(const uint4 *__restrict__ x, const __nv_bfloat16 *__restrict__ w, const float *__restrict__ bias,
+               __nv_bfloat16 *y, int n)
+{
+    __shared__ unsigned sx2[NH];   // channels 0-1 of the 10^3 halo cells
+    const int nt = n / TT, b = blockIdx.x;
+    const int x0 = (b % nt) * TT, y0 = ((b / nt) % nt) * TT, z0 = (b / (nt * nt)) * TT;
+    for (int h = threadIdx.x; h < NH; h += blockDim.x) {
+        const int hx = h % HT, hy = (h / HT) % HT, hz = h / (HT * HT);
+        const int64_t g = ((int64_t)wrapn(z0 - 1 + hz, n) * n + wrapn(y0 - 1 + hy, n)) * n + wrapn(x0 - 1 + hx, n);
+        sx2[h] = reinterpret_cast<const unsigned *>(x)[8 * g];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    // B fragments: k = 16 s + 2 t (+1) -> offset 8 s + t, channels 0, 1; k + 8 -> offset 8 s + t + 4
+    unsigned bf[4][2][2];
+#pragma unroll
+    for (int s4 = 0; s4 < 4; s4++)
+#pragma unroll
+        for (int nb = 0; nb < 2; nb++)
+#pragma unroll
+            for (int hfk = 0; hfk < 2; hfk++) {
+                const int oi = 8 * s4 + t + 4 * hfk;
+                bf[s4][nb][hfk] = oi < NOFF ? reinterpret_cast<const unsigned *>(w)[((oi * CH) + nb * 8 + g) * CH / 2] : 0u;
+            }
+    __syncthreads();
+    float acc[4][2][4] = {};
+#pragma unroll
+    for (int s4 = 0; s4 < 4; s4++) {
+        int hoff[2];
+#pragma unroll
+        for (int hfk = 0; hfk < 2; hfk++) {
+            const int oi = min(8 * s4 + t + 4 * hfk, NOFF - 1);   // zero-weight slots read any valid cell
+            const int dz = oi / 9 - 1, dy = (oi / 3) % 3 - 1, dx = oi % 3 - 1;
+            hoff[hfk] = ((warp + dz + 1) * HT + (dy + 1)) * HT + (g + dx + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            unsigned af[4];
+            af[0] = sx2[hoff[0] + (2 * j) * HT];       // row g (cy = 2j), k = 16 s + 2t
+            af[1] = sx2[hoff[0] + (2 * j + 1) * HT];   // row g + 8 (cy = 2j + 1)
+            af[2] = sx2[hoff[1] + (2 * j) * HT];       // row g, k + 8
+            af[3] = sx2[hoff[1] + (2 * j + 1) * HT];   // row g + 8, k + 8
+#pragma unroll
+            for (int nb = 0; nb < 2; nb++) mma_bf16(acc[j][nb], af, bf[s4][nb][0], bf[s4][nb][1]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int hf = 0; hf < 2; hf++) {
+            const int64_t cell = ((int64_t)(z0 + warp) * n + (y0 + 2 * j + hf)) * n + (x0 + g);
+#pragma unroll
+            for (int nb = 0; nb < 2; nb++) {
+                const int ch = nb * 8 + 2 * t;
+                const float v0 = fmaxf(acc[j][nb][2 * hf] + bias[ch], 0.f);
+                const float v1 = fmaxf(acc[j][nb][2 * hf + 1] + bias[ch + 1], 0.f);
+                reinterpret_cast<__nv_bfloat162 *>(y)[(cell * CH + ch) >> 1] = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+}
+
 // dw[d][co][ci] += sum_cells g[cell][co] x[cell + d][ci]; persistent CTAs over 8^3 tiles.
 // Warp w owns the offsets d = w, w + 8, w + 16 (and w + 24 for w < 3).
 __global__ void __launch_bounds__(CONV_THREADS, 2)
@@ -454,7 +520,10 @@ void conv_launch(pm_net *e, int layer, const __nv_bfloat16 *in, void *out, bool 
 
 void net_forward(pm_net *e)
 {
-    for (int l = 0; l < NL - 1; l++) conv_launch(e, l, e->act[l], e->act[l + 1], false, true, false);
+    const int ntiles = (e->n / TT) * (e->n / TT) * (e->n / TT);
+    k_conv_in2<<<ntiles, CONV_THREADS, 0, e->stream>>>(reinterpret_cast<const uint4 *>(e->act[0]), e->wf, e->bias,
+                                                       e->act[1], e->n);
+    for (int l = 1; l < NL - 1; l++) conv_launch(e, l, e->act[l], e->act[l + 1], false, true, false);
     conv_launch(e, NL - 1, e->act[NL - 1], e->out, false, false, true);
 }
 

@@ -355,6 +355,19 @@ def cpu_oracle_rate(n, steps, box):
     return n ** 3 * steps / dt, dt
 
 
+METRIC = "particle-updates/s per full PM step at 512^3 (mixed precision)"
+
+
+def workload_config(n, box, warmup, steps, world):
+    return {"workload": f"relativistic PM step, {n}^3 mesh, {n}^3 particles, box {box:.0f} Mpc/h, "
+                        f"LCDM Om={OM} h={H}, Zel'dovich/BBKS ICs z={ZI:.0f}, seed {SEED}, "
+                        f"steps {warmup}..{warmup + steps - 1} of a {N_STEPS_SCHEDULE}-step schedule",
+            "precision": "mixed: int32 cell + f32 offset, f32 fields/FFT, f64 background and k=0, "
+                         "compensated cell sums",
+            "components": "T00, 3 T0i, 5 trace-free Tij; phi, chi, B_i, h (2 helicities)",
+            "parallelism": f"replicas x{world}", "l2": "working set ~25 GB >> 129 MB L2, no flush"}
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle on bounded samples of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -376,14 +389,13 @@ def run_reference(args):
     value = n ** 3 * args.steps / dt
     sample = f"{args.steps} oracle steps of the same recipe at {n}^3 (box {box:.0f} Mpc/h, same cell size)"
     line = {
-        "impl": "reference", "metric": "particle-updates/s per full PM step", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "particle-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "relativistic PM step (FP64 CPU oracle) on a bounded sample of the 512^3 workload",
-                   "sample": sample},
+        "config": workload_config(args.n, CELL_MPCH * args.n, args.warmup, args.steps, args.gpus),
         "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample + "; the FP64 CPU oracle, single thread"},
         "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -559,19 +571,11 @@ def main():
     if rank == 0:
         h2d = 2 * 3 * 8 * n_part
         line = {
-            "metric": "particle-updates/s per full PM step at 512^3 (mixed precision)",
+            "metric": METRIC,
             "value": value, "unit": "particle-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"relativistic PM step, {n}^3 mesh, {n}^3 particles, box {box:.0f} Mpc/h, "
-                                   f"LCDM Om={OM} h={H}, Zel'dovich/BBKS ICs z={ZI:.0f}, seed {SEED}, "
-                                   f"steps {args.warmup}..{args.warmup + args.steps - 1} of a "
-                                   f"{N_STEPS_SCHEDULE}-step schedule",
-                       "precision": "mixed: int32 cell + f32 offset, f32 fields/FFT, f64 background and k=0, "
-                                    "compensated cell sums",
-                       "components": "T00, 3 T0i, 5 trace-free Tij; phi, chi, B_i, h (2 helicities)",
-                       "parallelism": f"replicas x{world}", "l2": "working set ~25 GB >> 129 MB L2, no flush",
-                       "ic_seconds": round(t_ic, 1)},
+            "config": dict(workload_config(n, box, args.warmup, args.steps, world), ic_seconds=round(t_ic, 1)),
             "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
             "kernels_roofline_frac": per_kernel_frac,
             "step_roofline_frac": survey_bytes_per_update(True) * n_part / (ms_max * 1e-3) / 1e9 / peak,

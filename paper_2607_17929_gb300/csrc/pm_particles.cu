@@ -688,21 +688,31 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_down(const int32_t *cnt, int64_
                                                        int32_t *start)
 {
     __shared__ int wt[33];
+    static_assert(SCAN_ITEMS == 4, "one 16-byte vector per thread");
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    const bool whole = base + SCAN_ITEMS <= n;   // 16-byte aligned: base is a multiple of 4 ints
     int v[SCAN_ITEMS], s = 0;
+    if (whole) {
+        const int4 q = *reinterpret_cast<const int4 *>(cnt + base);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; k++) {
-        int64_t i = base + k;
-        v[k] = i < n ? cnt[i] : 0;
-        s += v[k];
+        for (int k = 0; k < SCAN_ITEMS; k++) v[k] = base + k < n ? cnt[base + k] : 0;
     }
-    int tot;
-    int e = block_scan_1024(s, wt, &tot) + bsum[blockIdx.x];
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; k++) {
-        int64_t i = base + k;
-        if (i < n) start[i] = e;
-        e += v[k];
+    for (int k = 0; k < SCAN_ITEMS; k++) s += v[k];
+    int tot;
+    const int e = block_scan_1024(s, wt, &tot) + bsum[blockIdx.x];
+    const int o[SCAN_ITEMS] = {e, e + v[0], e + v[0] + v[1], e + v[0] + v[1] + v[2]};
+    if (whole) {
+        *reinterpret_cast<int4 *>(start + base) = make_int4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++)
+            if (base + k < n) start[base + k] = o[k];
     }
 }
 

@@ -296,9 +296,8 @@ template <class T> size_t cols_smem(int n, int L)
 
 template <class T> void set_smem_attrs()
 {
-    static bool done = false;
-    if (done) return;
-    done = true;
+    static std::atomic<uint64_t> done{0};
+    if (!first_on_device(done)) return;
     const int maxs = 160 * 1024;
     cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
     cudaFuncSetAttribute(k_fft_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
@@ -491,9 +490,8 @@ k_c2r_fast(const __grid_constant__ Ptrs in, const __grid_constant__ Ptrs out, co
 template <class T, int N> struct FastPasses {
     static void attrs()
     {
-        static bool done = false;
-        if (done) return;
-        done = true;
+        static std::atomic<uint64_t> done{0};
+        if (!first_on_device(done)) return;
         auto set = [](auto k, size_t b) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); };
         set(k_col_fast<T, N, -1, false>, col_fast_smem<T, N, false>());
         set(k_col_fast<T, N, 1, false>, col_fast_smem<T, N, false>());

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -145,6 +146,16 @@ struct Ctx {
 // Event points inside one step.
 enum { EV_START = 0, EV_PROJECT = 1, EV_FWD_X = 2, EV_FWD_Y = 3, EV_FWD_Z = 4, EV_SOLVE = 5,
        EV_INV_Z = 6, EV_INV_Y = 7, EV_INV_X = 8, EV_KICK = 9, EV_SCAN = 10, EV_END = 11 };
+
+// True the first time it is called with `mask` on the current device (for per-device one-time set-up
+// such as kernel attributes; a repeated set-up from a racing thread is harmless).
+inline bool first_on_device(std::atomic<uint64_t> &mask)
+{
+    int d = 0;
+    cudaGetDevice(&d);
+    const uint64_t bit = 1ull << (d & 63);
+    return (mask.fetch_or(bit) & bit) == 0;
+}
 
 // ---------------------------------------------------------------------------
 // Launchers (implemented in pm_fft.cu, pm_particles.cu, pm_solve.cu).

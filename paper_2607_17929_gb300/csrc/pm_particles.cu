@@ -866,10 +866,9 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 template <class T>
 void launch_project(Ctx &c, const StepScalars &s)
 {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr{0};
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dep_smem<T>());
-        attr = true;
     }
     DepParams<T> p{};
     p.part = reinterpret_cast<const Particle<T> *>(c.part[c.cur]);
@@ -917,10 +916,9 @@ void launch_project(Ctx &c, const StepScalars &s)
 template <class T>
 void launch_kick_drift(Ctx &c, const StepScalars &s)
 {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr{0};
+    if (first_on_device(attr)) {
         cudaFuncSetAttribute(k_kick_drift<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kd_smem<T>());
-        attr = true;
     }
     KdParams<T> p{};
     p.part = reinterpret_cast<Particle<T> *>(c.part[c.cur]);

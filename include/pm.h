@@ -270,9 +270,14 @@ pm_status pm_ensemble_sync(pm_ensemble *e);
  * streams wait on it.  Owned by the ensemble. */
 pm_status pm_ensemble_stream(pm_ensemble *e, void **stream);
 
-/* Autotuner: times one graph-captured ensemble step for each candidate number
- * of streams (1, 2, 4, ... up to nbox, at most 32) and keeps the fastest;
- * *n_streams receives it.  Each trial advances every box by one step. */
+/* Use n_streams streams (1 .. 32) from the next step on.  With more than one,
+ * the boxes of the largest mesh run in order on the first stream and the
+ * smaller boxes round-robin on the others. */
+pm_status pm_ensemble_set_streams(pm_ensemble *e, int32_t n_streams);
+
+/* Autotuner: for each candidate number of streams (1, 2, 4, 8, at most nbox)
+ * runs one untimed and two timed graph-captured ensemble steps and keeps the
+ * fastest; *n_streams receives it.  Each trial advances every box by three steps. */
 pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams);
 
 /* ------------------------------------------------------------------------

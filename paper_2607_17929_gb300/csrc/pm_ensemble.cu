@@ -3,11 +3,15 @@
 // ensemble step issues all boxes' steps on K streams and captures them into
 // one CUDA graph, so the small boxes' kernels run concurrently and the CPU
 // issues one graph launch per step.  K is chosen by pm_ensemble_tune, which
-// times ensemble steps for a few candidate stream counts.  The step is
+// times ensemble steps for a few candidate stream counts.  With K > 1 the
+// boxes of the largest mesh go, in order, to stream 0, whose large grids fill
+// the GPU anyway; the smaller boxes spread over streams 1 .. K-1, so that
+// their small, launch-bound kernels run beside the large ones.  The step is
 // captured afresh each time (the potential ring, the particle ping-pong and
 // the step's scalars change from step to step) but the topology does not, so
 // the executable graph of the previous step is updated in place rather than
 // instantiated again.
+#include <algorithm>
 #include <chrono>
 #include <vector>
 
@@ -23,7 +27,18 @@ struct pm_ensemble {
     cudaGraphExec_t exec = nullptr;  // executable graph of the last captured step
     int exec_k = 0;                  // stream count it was captured with
     int k = 1;                       // streams in use
+    int nmax = 0;                    // largest mesh side in the ensemble
     std::string err;
+
+    // stream of box b for the current stream count
+    cudaStream_t stream_of(size_t b) const
+    {
+        if (k == 1) return streams[0];
+        if (box[b]->c.N == nmax) return streams[0];
+        size_t r = 0;   // rank of b among the smaller boxes
+        for (size_t i = 0; i < b; i++) r += box[i]->c.N != nmax;
+        return streams[1 + r % (size_t)(k - 1)];
+    }
 };
 
 namespace {
@@ -49,7 +64,7 @@ pm_status ens_issue(pm_ensemble *e, bool capture)
     pm_status st = PM_OK;
     for (size_t b = 0; b < e->box.size() && st == PM_OK; b++) {
         pm::Ctx &c = e->box[b]->c;
-        c.stream = e->streams[b % e->k];
+        c.stream = e->stream_of(b);
         c.no_timing = capture;
         st = pm_step(e->box[b]);
         c.no_timing = false;
@@ -112,9 +127,10 @@ pm_status pm_ensemble_init(const pm_config *cfgs, int32_t nbox, pm_ensemble **ou
         return PM_ERR_CUDA;
     }
     e->k = nbox < 8 ? nbox : 8;
+    for (int b = 0; b < nbox; b++) e->nmax = std::max(e->nmax, (int)cfgs[b].n_mesh);
     for (int b = 0; b < nbox; b++) {
         pm_config cfg = cfgs[b];
-        cfg.stream = e->streams[b % e->k];
+        cfg.stream = e->streams[0];
         pm_ctx *c = nullptr;
         pm_status st = pm_init(&cfg, &c);
         if (st != PM_OK) {
@@ -161,7 +177,7 @@ pm_status pm_ensemble_set_particles(pm_ensemble *e, int32_t box, const double *p
 {
     if (!e || box < 0 || box >= (int32_t)e->box.size()) return PM_ERR_INVALID_ARG;
     pm_ctx *c = e->box[box];
-    c->c.stream = e->streams[box % e->k];
+    c->c.stream = e->stream_of((size_t)box);
     pm_status st = pm_set_particles(c, pos, mom);
     if (st == PM_OK && cudaStreamSynchronize(c->c.stream) != cudaSuccess) return PM_ERR_CUDA;
     return st;
@@ -190,19 +206,32 @@ pm_status pm_ensemble_stream(pm_ensemble *e, void **stream)
     return PM_OK;
 }
 
+pm_status pm_ensemble_set_streams(pm_ensemble *e, int32_t n_streams)
+{
+    if (!e || n_streams < 1 || n_streams > ENS_MAX_STREAMS) return PM_ERR_INVALID_ARG;
+    e->k = n_streams;
+    return PM_OK;
+}
+
 pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams)
 {
     if (!e) return PM_ERR_INVALID_ARG;
-    const int cand[] = {1, 2, 4, 8, 16, 32};
+    const int cand[] = {1, 2, 4, 8};
+    constexpr int TRIAL_STEPS = 2;
     float best = 1e30f;
     int best_k = e->k;
     for (int k : cand) {
         if (k > (int)e->box.size() || k > ENS_MAX_STREAMS) break;
-        // a trial step per candidate (the boxes advance: tuning consumes schedule steps)
+        // one untimed step (it instantiates the graph of the new stream layout), then TRIAL_STEPS timed
+        // graph steps (the boxes advance: tuning consumes schedule steps)
         e->k = k;
+        pm_status st0 = pm_ensemble_step(e, 1);
+        if (st0 != PM_OK) return st0;
         if (cudaEventRecord(e->t0, e->origin) != cudaSuccess) return PM_ERR_CUDA;
-        pm_status st = pm_ensemble_step(e, 1);
-        if (st != PM_OK) return st;
+        for (int t = 0; t < TRIAL_STEPS; t++) {
+            pm_status st = pm_ensemble_step(e, 1);
+            if (st != PM_OK) return st;
+        }
         cudaEventRecord(e->t1, e->origin);
         if (cudaEventSynchronize(e->t1) != cudaSuccess) return PM_ERR_CUDA;
         float ms = 0.f;

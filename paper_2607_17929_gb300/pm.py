@@ -72,6 +72,7 @@ def _load():
         "pm_ensemble_sync": ([vp], C.c_int),
         "pm_ensemble_tune": ([vp, C.POINTER(i32)], C.c_int),
         "pm_ensemble_stream": ([vp, C.POINTER(vp)], C.c_int),
+        "pm_ensemble_set_streams": ([vp, i32], C.c_int),
         "pm_power_spectrum_noalloc": ([vp, i64, i32, C.c_double, i32, dp, dp, C.POINTER(i64), vp], C.c_int),
         "pm_net_param_count": ([], i64),
         "pm_net_create": ([i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
@@ -107,7 +108,7 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_update", "pm_step", "pm_put_particles", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
             "pm_power_spectrum_noalloc", "pm_ensemble_init", "pm_ensemble_destroy", "pm_ensemble_last_error",
             "pm_ensemble_box", "pm_ensemble_set_particles", "pm_ensemble_step", "pm_ensemble_sync", "pm_ensemble_tune",
-            "pm_ensemble_stream", "pm_net_param_count", "pm_net_create", "pm_net_destroy", "pm_net_last_error",
+            "pm_ensemble_stream", "pm_ensemble_set_streams", "pm_net_param_count", "pm_net_create", "pm_net_destroy", "pm_net_last_error",
             "pm_net_set_params", "pm_net_get_params", "pm_net_buffer", "pm_net_features", "pm_net_target",
             "pm_net_forward", "pm_net_backward", "pm_net_adam", "pm_net_train_step", "pm_net_apply",
             "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight",
@@ -302,6 +303,10 @@ def pm_ensemble_stream(e):
     h = C.c_void_p()
     _echeck(e, lib.pm_ensemble_stream(e, C.byref(h)))
     return h.value or 0
+
+
+def pm_ensemble_set_streams(e, n_streams):
+    _echeck(e, lib.pm_ensemble_set_streams(e, int(n_streams)))
 
 
 def pm_ensemble_tune(e):

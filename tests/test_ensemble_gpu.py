@@ -78,12 +78,12 @@ def test_mixed_ensemble_matches_boxes_stepped_alone_and_tunes(pm):
         g.set_particles(pos, mom)
         alone.append(g)
     pm.pm_ensemble_step(e, use_graph=False)
-    k = pm.pm_ensemble_tune(e)  # 1, 2, 4 streams: three more steps
+    k = pm.pm_ensemble_tune(e)  # 1, 2, 4 streams, three steps each
     assert k in (1, 2, 4)
     pm.pm_ensemble_step(e, use_graph=True)
     pm.pm_ensemble_sync(e)
     for b, (n, box, _) in enumerate(specs):
-        for _ in range(5):
+        for _ in range(1 + 3 * 3 + 1):
             alone[b].step()
         pos, mom, phi = _box_state(pm, e, b, n)
         pa, ua = alone[b].particles()

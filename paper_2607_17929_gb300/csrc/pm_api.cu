@@ -2,6 +2,7 @@
 // host/device I/O and checkpoints.  See include/pm.h for the contract.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -628,8 +629,13 @@ pm_status pm_init(const pm_config *cfg, pm_ctx **out)
         {(void **)&c.dscal, sizeof(double) * (8 + 1024)},
         {&c.stage_buf, sizeof(double) * (size_t)c.stage_elems},
     };
+    // PM_TEST_FAIL_ALLOC=k (test hook): the k-th device allocation of this call reports failure, to
+    // exercise the clean-up path without exhausting the device
+    const char *fail_env = std::getenv("PM_TEST_FAIL_ALLOC");
+    const int fail_at = fail_env ? std::atoi(fail_env) : 0;
+    int nalloc = 0;
     for (const A &a : allocs) {
-        if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+        if (++nalloc == fail_at || cudaMalloc(a.p, a.bytes) != cudaSuccess) {
             cudaGetLastError();
             pm_destroy(ctx);
             return PM_ERR_OOM;

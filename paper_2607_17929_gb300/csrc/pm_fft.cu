@@ -325,13 +325,13 @@ void col_pass(Ctx &c, int nf, const Ptrs &p, int64_t stride_j, int64_t ncols, in
 // lines per block (line width sets the contiguous row segment) and the threads
 // per SM the register budget must allow.  Chosen by timing at 512^3.
 #ifndef PM_COLY_P
-#define PM_COLY_P 8
+#define PM_COLY_P 32
 #endif
 #ifndef PM_COLY_L
 #define PM_COLY_L 8
 #endif
 #ifndef PM_COLY_TPSM
-#define PM_COLY_TPSM 1536
+#define PM_COLY_TPSM 512
 #endif
 #ifndef PM_COLZ_P
 #define PM_COLZ_P 16

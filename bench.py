@@ -66,7 +66,7 @@ def kernel_bytes(name, n, n_part, mixed):
     }[name]
 
 
-def survey_bytes_per_update(mixed):
+def method_bytes_per_update(mixed):
     """Minimum bytes per particle update of the method (140 B/particle + 288 B/cell mixed; twice for FP64)."""
     return 428.0 if mixed else 816.0
 
@@ -518,7 +518,7 @@ def main():
         fp64 = {"ms_per_step": ms64, "value": world * n_part / (ms64 * 1e-3),
                 "speedup_mixed_over_fp64": ms64 / ms_max,
                 "kernels_ms": {k: round(v, 4) for k, v in kern64.items()},
-                "step_roofline_frac": survey_bytes_per_update(False) * n_part / (ms64 * 1e-3) / 1e9 /
+                "step_roofline_frac": method_bytes_per_update(False) * n_part / (ms64 * 1e-3) / 1e9 /
                 load_peaks()[0]}
         del sim64
     torch.cuda.empty_cache()
@@ -578,7 +578,7 @@ def main():
             "config": dict(workload_config(n, box, args.warmup, args.steps, world), ic_seconds=round(t_ic, 1)),
             "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
             "kernels_roofline_frac": per_kernel_frac,
-            "step_roofline_frac": survey_bytes_per_update(True) * n_part / (ms_max * 1e-3) / 1e9 / peak,
+            "step_roofline_frac": method_bytes_per_update(True) * n_part / (ms_max * 1e-3) / 1e9 / peak,
             "design_bytes_per_step": design_bytes,
             "design_roofline_frac": design_bytes / (ms_max * 1e-3) / 1e9 / peak,
             "roofline": roofline,

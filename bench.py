@@ -333,6 +333,69 @@ def correction_bench(pm, torch, reps=20):
                                  "burst peak"}}
 
 
+def _load_cufft():
+    import ctypes
+    import glob
+    import torch
+    names = ["libcufft.so.12", "libcufft.so"]
+    names += glob.glob(os.path.join(os.path.dirname(torch.__file__), "..", "nvidia", "*", "lib", "libcufft.so*"))
+    names += glob.glob("/usr/local/cuda/lib64/libcufft.so*")
+    for nm in names:
+        try:
+            return ctypes.CDLL(nm)
+        except OSError:
+            continue
+    return None
+
+
+def cufft_bench(torch, n, reps=5):
+    """cuFFT on the transforms one step makes: batched r2c of the 9 source fields and c2r of the 5 force
+    fields, n^3, out of place (c2r overwrites its input; the values do not change the timing).  A
+    comparison for the hand-written passes only; the step never calls it."""
+    import ctypes
+    lib = _load_cufft()
+    if lib is None:
+        return {"unavailable": "libcufft not found"}
+    R2C, C2R, D2Z, Z2D = 0x2A, 0x2C, 0x6A, 0x6C
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, dt, kf, ki in (("f32", torch.float32, R2C, C2R), ("f64", torch.float64, D2Z, Z2D)):
+        x = torch.randn((9, n, n, n), dtype=dt, device="cuda")
+        X = torch.empty((9, n, n, n // 2 + 1), dtype=torch.complex64 if dt == torch.float32 else torch.complex128,
+                        device="cuda")
+        dims = (ctypes.c_int * 3)(n, n, n)
+        plans = []
+        for kind, batch in ((kf, 9), (ki, 5)):
+            h = ctypes.c_int()
+            rc = lib.cufftPlanMany(ctypes.byref(h), 3, dims, None, 1, 0, None, 1, 0, kind, batch)
+            if rc != 0:
+                return {"unavailable": f"cufftPlanMany returned {rc}"}
+            lib.cufftSetStream(h, ctypes.c_void_p(stream.cuda_stream))
+            plans.append(h)
+        execf = lib.cufftExecR2C if dt == torch.float32 else lib.cufftExecD2Z
+        execi = lib.cufftExecC2R if dt == torch.float32 else lib.cufftExecZ2D
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        res = {}
+        for key, fn in (("fwd_ms", lambda: execf(plans[0], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(X.data_ptr()))),
+                        ("inv_ms", lambda: execi(plans[1], ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(x.data_ptr())))):
+            for _ in range(3):
+                if fn() != 0:
+                    return {"unavailable": f"cuFFT exec failed ({name} {key})"}
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            res[key] = round(ev0.elapsed_time(ev1) / reps, 4)
+        for h in plans:
+            lib.cufftDestroy(h)
+        out[name] = res
+        del x, X
+        torch.cuda.empty_cache()
+    return out
+
+
 def load_bf16_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -415,6 +478,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-correction", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=10)
     args = ap.parse_args()
@@ -542,6 +606,15 @@ def main():
         correction = correction_bench(pm, torch)
         torch.cuda.empty_cache()
 
+    cufft = None
+    if not args.no_cufft:
+        cufft = cufft_bench(torch, n)
+        cufft["ours_f32"] = {"fwd_ms": round(kern["fft_fwd"], 4), "inv_ms": round(kern["fft_inv"], 4)}
+        if fp64 is not None:
+            cufft["ours_f64"] = {"fwd_ms": fp64["kernels_ms"]["fft_fwd"], "inv_ms": fp64["kernels_ms"]["fft_inv"]}
+        cufft["what"] = (f"batched 9 r2c and 5 c2r transforms of {n}^3, out of place, cuFFT plans made once; "
+                         "comparison only (the step runs the hand-written passes)")
+
     ensemble = None
     if not args.no_ensemble:
         ensemble = ensemble_bench(pm, torch, args.ensemble_steps, 3)
@@ -586,6 +659,7 @@ def main():
             "variants": variants,
             "ensemble": ensemble,
             "correction": correction,
+            "cufft_comparison": cufft,
             "e2e": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                     "how": "pm_put_particles(pinned host f64 pos, mom) + pm_step + pm_get_particles(pinned host)"},

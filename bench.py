@@ -333,6 +333,32 @@ def correction_bench(pm, torch, reps=20):
                                  "burst peak"}}
 
 
+def schedule_phases(pm, torch, n, n_part, box, d_pos, d_mom, stream, block=10):
+    """The whole 100-step schedule (z = 100 -> 0) in blocks of `block` steps, each timed with CUDA events
+    with its per-kernel means: clustering makes late steps costlier for the deposit and the sort."""
+    sim = pm.PM(n, n_part, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED, 0, stream)
+    sim.set_particles(d_pos, d_mom)
+    a_n, _, _ = sim.schedule()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for b0 in range(0, N_STEPS_SCHEDULE, block):
+        k = min(block, N_STEPS_SCHEDULE - b0)
+        torch.cuda.synchronize()
+        pm.pm_get_timings(sim.ctx)
+        ev0.record(stream)
+        for _ in range(k):
+            sim.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        per_kernel, _ = pm.pm_get_timings(sim.ctx)
+        out.append({"steps": f"{b0}-{b0 + k - 1}", "z": [round(1 / a_n[b0] - 1, 2), round(1 / a_n[b0 + k - 1] - 1, 3)],
+                    "ms_per_step": round(ev0.elapsed_time(ev1) / k, 3),
+                    "kernels_ms": {key: round(per_kernel[key], 3) for key in
+                                   ("project", "fft_fwd", "solve", "fft_inv", "kick_drift", "sort")}})
+    sim.close()
+    return out
+
+
 def _load_cufft():
     import ctypes
     import glob
@@ -479,6 +505,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-correction", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-phases", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=10)
     args = ap.parse_args()
@@ -573,6 +600,12 @@ def main():
     sim.close()
     del sim
 
+    # the whole schedule in blocks of 10 steps (early vs late, clustered steps)
+    phases = None
+    if not args.no_phases:
+        phases = schedule_phases(pm, torch, n, n_part, box, d_pos, d_mom, stream)
+        torch.cuda.empty_cache()
+
     # FP64 path on the same workload
     fp64 = None
     if not args.no_fp64:
@@ -660,6 +693,7 @@ def main():
             "ensemble": ensemble,
             "correction": correction,
             "cufft_comparison": cufft,
+            "schedule_phases": phases,
             "e2e": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                     "how": "pm_put_particles(pinned host f64 pos, mom) + pm_step + pm_get_particles(pinned host)"},

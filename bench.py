@@ -243,6 +243,10 @@ def ensemble_bench(pm, torch, steps, warmup):
         pm.pm_ensemble_set_particles(e, b, p, u)
     pm.pm_ensemble_step(e, use_graph=False)
     k = pm.pm_ensemble_tune(e)
+    shapes = {}
+    for b, (n, _, _) in enumerate(specs):
+        if n not in shapes:
+            shapes[n] = pm.pm_fft_shapes(pm.pm_ensemble_box(e, b), -2, -2)
     es = torch.cuda.ExternalStream(pm.pm_ensemble_stream(e))
     for _ in range(warmup):
         pm.pm_ensemble_step(e, use_graph=True)
@@ -271,6 +275,7 @@ def ensemble_bench(pm, torch, steps, warmup):
     return {"metric": "boxes*steps/s", "value": nb / (ens_ms * 1e-3), "ms_per_step": ens_ms,
             "host_wall_ms_per_step": wall_ms, "loop_value": nb / (loop_ms * 1e-3), "loop_ms_per_step": loop_ms,
             "speedup_over_loop": loop_ms / ens_ms, "streams": k, "no_graph_ms_per_step": nog_ms,
+            "fft_shapes": {str(n): list(v) for n, v in shapes.items()},
             "particle_updates_per_s": part / (ens_ms * 1e-3), "steps": steps, "warmup": warmup,
             "config": "48 boxes: 16 x 64^3, 16 x 128^3, 16 x 192^3 mesh, one particle per cell, box U(200,1000) "
                       "Mpc/h, seeds 1000+b, mixed precision, same Zel'dovich/BBKS recipe at z=100",

@@ -227,6 +227,21 @@ pm_status pm_get_schedule(pm_ctx *ctx, double *a_n, double *dtau, double *a_half
  * in that window. */
 pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n, int64_t *launches);
 
+/* Shapes of the y and z column passes of the FFT.  Mixed-precision contexts
+ * with N = 64, 128, 256 or 512 have three shapes per pass (points per thread,
+ * lines per block):
+ *   y pass: 0 = (32, 8), 1 = (16, 8), 2 = (8, 8);
+ *   z pass: 0 = (16, 16), 1 = (8, 16), 2 = (16, 8).
+ * Shape 0 of each pass is the default.  force_y / force_z in 0..2 select a
+ * shape; -2 keeps the current one; -1 times the three shapes of that pass on
+ * the context's own spectrum buffers (the 9 forward and 5 inverse line
+ * transforms of a step; these buffers hold nothing between steps, they are
+ * cleared first) and keeps the fastest.  Every shape computes the same transform in the same arithmetic
+ * order.  *y_shape / *z_shape (may be NULL) receive the shapes in use.
+ * Contexts without a choice (FP64, other N) keep shape 0 and return PM_OK.
+ * Errors: INVALID_ARG (force_* outside -2..2), STATE, CUDA. */
+pm_status pm_fft_shapes(pm_ctx *ctx, int32_t force_y, int32_t force_z, int32_t *y_shape, int32_t *z_shape);
+
 /* Checkpoint: write / read the full state (config, step, particles,
  * phi_{n-1}, chi_{n-1}, phi_{n-2}, tensor state) to / from a host file.
  * pm_load requires a context created with the same config.
@@ -275,9 +290,12 @@ pm_status pm_ensemble_stream(pm_ensemble *e, void **stream);
  * smaller boxes round-robin on the others. */
 pm_status pm_ensemble_set_streams(pm_ensemble *e, int32_t n_streams);
 
-/* Autotuner: for each candidate number of streams (1, 2, 4, 8, at most nbox)
- * runs one untimed and two timed graph-captured ensemble steps and keeps the
- * fastest; *n_streams receives it.  Each trial advances every box by three steps. */
+/* Autotuner: first the FFT column-pass shapes of every distinct mesh size
+ * (pm_fft_shapes with -1 on the first box of that size, the choice copied to
+ * the others; no box advances), then for each candidate number of streams
+ * (1, 2, 4, 8, at most nbox) one untimed and two timed graph-captured
+ * ensemble steps, keeping the fastest; *n_streams receives it.  Each stream
+ * trial advances every box by three steps. */
 pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams);
 
 /* ------------------------------------------------------------------------

@@ -866,6 +866,24 @@ pm_status pm_get_schedule(pm_ctx *ctx, double *a_n, double *dtau, double *a_half
     return PM_OK;
 }
 
+pm_status pm_fft_shapes(pm_ctx *ctx, int32_t force_y, int32_t force_z, int32_t *y_shape, int32_t *z_shape)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (force_y < -2 || force_y > 2 || force_z < -2 || force_z > 2)
+        return fail(c, PM_ERR_INVALID_ARG, "pm_fft_shapes: shape outside -2..2");
+    if (force_y == -2) force_y = c.col_shape[0];
+    if (force_z == -2) force_z = c.col_shape[1];
+    PM_DISPATCH(ctx, fft_tune_shapes, c, force_y, force_z);
+    cudaError_t e = c.stream ? cudaStreamSynchronize(c.stream) : cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "pm_fft_shapes");
+    if (y_shape) *y_shape = c.col_shape[0];
+    if (z_shape) *z_shape = c.col_shape[1];
+    return PM_OK;
+}
+
 pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n, int64_t *launches)
 {
     pm_status g = guard(ctx);

@@ -216,6 +216,21 @@ pm_status pm_ensemble_set_streams(pm_ensemble *e, int32_t n_streams)
 pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams)
 {
     if (!e) return PM_ERR_INVALID_ARG;
+    // FFT column-pass shapes, once per distinct mesh size
+    for (size_t b = 0; b < e->box.size(); b++) {
+        pm::Ctx &c = e->box[b]->c;
+        size_t first = b;
+        for (size_t a = 0; a < b; a++)
+            if (e->box[a]->c.N == c.N && e->box[a]->c.mixed == c.mixed) {
+                first = a;
+                break;
+            }
+        c.stream = e->stream_of(b);
+        pm_status st = first == b ? pm_fft_shapes(e->box[b], -1, -1, nullptr, nullptr)
+                                  : pm_fft_shapes(e->box[b], e->box[first]->c.col_shape[0],
+                                                  e->box[first]->c.col_shape[1], nullptr, nullptr);
+        if (st != PM_OK) return st;
+    }
     const int cand[] = {1, 2, 4, 8};
     constexpr int TRIAL_STEPS = 2;
     float best = 1e30f;

@@ -320,50 +320,38 @@ void col_pass(Ctx &c, int nf, const Ptrs &p, int64_t stride_j, int64_t ncols, in
 // ---------------------------------------------------------------------------
 // Compile-time-N passes (register-resident radix stages, see pm_fft_core.cuh).
 // ---------------------------------------------------------------------------
-// Shape of the FP32 column passes for power-of-two sizes >= 64 (ZP: the z pass,
-// whose points are a whole plane apart, else the y pass): points per thread,
-// lines per block (line width sets the contiguous row segment) and the threads
-// per SM the register budget must allow.  Chosen by timing at 512^3.
-#ifndef PM_COLY_P
-#define PM_COLY_P 32
-#endif
-#ifndef PM_COLY_L
-#define PM_COLY_L 8
-#endif
-#ifndef PM_COLY_TPSM
-#define PM_COLY_TPSM 512
-#endif
-#ifndef PM_COLZ_P
-#define PM_COLZ_P 16
-#endif
-#ifndef PM_COLZ_L
-#define PM_COLZ_L 16
-#endif
-#ifndef PM_COLZ_TPSM
-#define PM_COLZ_TPSM 1024
-#endif
+// Shapes of the FP32 column passes for power-of-two sizes >= 64 (ZP: the z
+// pass, whose points are a whole plane apart, else the y pass): points per
+// thread, lines per block (the line width sets the contiguous row segment)
+// and the threads per SM the register budget must allow.  Shape 0 is the one
+// timed best at 512^3; fft_tune_shapes picks among the three per context.
+struct ColShape {
+    int p, l, tpsm;
+};
+constexpr int NCOLSHAPES = 3;
+constexpr ColShape kColY[NCOLSHAPES] = {{32, 8, 512}, {16, 8, 1024}, {8, 8, 1536}};
+constexpr ColShape kColZ[NCOLSHAPES] = {{16, 16, 1024}, {8, 16, 1536}, {16, 8, 1024}};
 
-template <class T, int N, bool ZP = false> struct Lines {
+template <class T, int N, bool ZP = false, int V = 0> struct Lines {
     static constexpr bool tuned = sizeof(T) == 4 && N % 3 != 0 && N >= 64;
-    static constexpr int PP = ZP ? PM_COLZ_P : PM_COLY_P;
-    static constexpr int CP = tuned && PP != 8 ? PP : 0;  // 0: default points per thread
+    static constexpr ColShape sh = ZP ? kColZ[V] : kColY[V];
+    static constexpr int CP = tuned && sh.p != 8 ? sh.p : 0;  // 0: default points per thread
     static constexpr int TL = fftc::Geo<N>::TL;
     static constexpr int TLC = fftc::Geo<N, CP>::TL;
     // lines per block of the column passes: 64-byte row segments by default, >= 128 threads
-    static constexpr int col0 = tuned ? (ZP ? PM_COLZ_L : PM_COLY_L) : (sizeof(T) == 4 ? 8 : 4);
+    static constexpr int col0 = tuned ? sh.l : (sizeof(T) == 4 ? 8 : 4);
     static constexpr int col1 = col0 * TLC < 128 ? 128 / TLC : col0;
     static constexpr int col = col1 * TLC > 1024 ? 1024 / TLC : col1;
     static constexpr int row = TL >= 256 ? 1 : 256 / TL;               // row pairs per block, x passes
     // resident blocks per SM the register allocation must allow
-    static constexpr int tpsm = tuned ? (ZP ? PM_COLZ_TPSM : PM_COLY_TPSM)
-                                      : (fftc::Geo<N>::P == 8 ? (sizeof(T) == 4 ? 1536 : 1024) : 0);
+    static constexpr int tpsm = tuned ? sh.tpsm : (fftc::Geo<N>::P == 8 ? (sizeof(T) == 4 ? 1536 : 1024) : 0);
     static constexpr int col_min_blocks = tpsm / (TLC * col) > 0 ? tpsm / (TLC * col) : 1;
 };
 
-template <class T, int N, bool ZP> size_t col_fast_smem()
+template <class T, int N, bool ZP, int V> size_t col_fast_smem()
 {
     using G = fftc::Geo<N>;
-    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)N * Lines<T, N, ZP>::col);  // TWN does not depend on P
+    return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)N * Lines<T, N, ZP, V>::col);  // TWN does not depend on P
 }
 template <class T, int N> size_t row_fast_smem()
 {
@@ -371,15 +359,15 @@ template <class T, int N> size_t row_fast_smem()
     return sizeof(typename Cplx<T>::type) * (G::TWN + (size_t)Lines<T, N>::row * fftc::RowIdx<N>::pitch);
 }
 
-template <class T, int N, int DIR, bool ZP>
-__global__ void __launch_bounds__(Lines<T, N, ZP>::TLC * Lines<T, N, ZP>::col, Lines<T, N, ZP>::col_min_blocks)
+template <class T, int N, int DIR, bool ZP, int V>
+__global__ void __launch_bounds__(Lines<T, N, ZP, V>::TLC * Lines<T, N, ZP, V>::col, Lines<T, N, ZP, V>::col_min_blocks)
 k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t stride_j,
            int64_t ncols, int64_t stride_b, int64_t nlines)
 {
     using C = typename Cplx<T>::type;
-    constexpr int CP = Lines<T, N, ZP>::CP;
+    constexpr int CP = Lines<T, N, ZP, V>::CP;
     using G = fftc::Geo<N, CP>;
-    constexpr int L = Lines<T, N, ZP>::col;
+    constexpr int L = Lines<T, N, ZP, V>::col;
     extern __shared__ __align__(16) unsigned char smem[];
     C *tw = reinterpret_cast<C *>(smem);
     C *buf = tw + G::TWN;
@@ -493,31 +481,51 @@ template <class T, int N> struct FastPasses {
         static std::atomic<uint64_t> done{0};
         if (!first_on_device(done)) return;
         auto set = [](auto k, size_t b) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); };
-        set(k_col_fast<T, N, -1, false>, col_fast_smem<T, N, false>());
-        set(k_col_fast<T, N, 1, false>, col_fast_smem<T, N, false>());
-        set(k_col_fast<T, N, -1, true>, col_fast_smem<T, N, true>());
-        set(k_col_fast<T, N, 1, true>, col_fast_smem<T, N, true>());
+        set_col<0>();
+        if constexpr (Lines<T, N>::tuned) {
+            set_col<1>();
+            set_col<2>();
+        }
         set(k_r2c_fast<T, N>, row_fast_smem<T, N>());
         set(k_c2r_fast<T, N>, row_fast_smem<T, N>());
     }
-    template <bool ZP> static void cols_t(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    template <int V> static void set_col()
     {
-        constexpr int L = Lines<T, N, ZP>::col;
-        constexpr int threads = Lines<T, N, ZP>::TLC * L;
+        auto set = [](auto k, size_t b) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); };
+        set(k_col_fast<T, N, -1, false, V>, col_fast_smem<T, N, false, V>());
+        set(k_col_fast<T, N, 1, false, V>, col_fast_smem<T, N, false, V>());
+        set(k_col_fast<T, N, -1, true, V>, col_fast_smem<T, N, true, V>());
+        set(k_col_fast<T, N, 1, true, V>, col_fast_smem<T, N, true, V>());
+    }
+    template <bool ZP, int V>
+    static void cols_t(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    {
+        constexpr int L = Lines<T, N, ZP, V>::col;
+        constexpr int threads = Lines<T, N, ZP, V>::TLC * L;
         dim3 grid((unsigned)((nl + L - 1) / L), nf);
         const auto *tw = reinterpret_cast<const typename Cplx<T>::type *>(c.tw2);
-        const size_t sm = col_fast_smem<T, N, ZP>();
+        const size_t sm = col_fast_smem<T, N, ZP, V>();
         if (dir < 0)
-            k_col_fast<T, N, -1, ZP><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
+            k_col_fast<T, N, -1, ZP, V><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
         else
-            k_col_fast<T, N, 1, ZP><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
+            k_col_fast<T, N, 1, ZP, V><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
         c.launches++;
+    }
+    template <bool ZP>
+    static void cols_v(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    {
+        const int v = Lines<T, N>::tuned ? c.col_shape[ZP ? 1 : 0] : 0;
+        if constexpr (Lines<T, N>::tuned) {
+            if (v == 1) return cols_t<ZP, 1>(c, nf, p, sj, nc, sb, nl, dir);
+            if (v == 2) return cols_t<ZP, 2>(c, nf, p, sj, nc, sb, nl, dir);
+        }
+        cols_t<ZP, 0>(c, nf, p, sj, nc, sb, nl, dir);
     }
     // a z pass has no batch stride (its lines are the whole (ky, kx) plane)
     static void cols(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
     {
-        if (sb == 0) cols_t<true>(c, nf, p, sj, nc, sb, nl, dir);
-        else cols_t<false>(c, nf, p, sj, nc, sb, nl, dir);
+        if (sb == 0) cols_v<true>(c, nf, p, sj, nc, sb, nl, dir);
+        else cols_v<false>(c, nf, p, sj, nc, sb, nl, dir);
     }
     static void rows(Ctx &c, int nf, const Ptrs &pi, const Ptrs &po, int dir)
     {
@@ -622,6 +630,83 @@ void fft_inverse(Ctx &c, int nf, void *const *spec_in, void *const *real_out)
     c.launches++;
     c.mark(EV_INV_X);
 }
+
+template <class T>
+bool fft_shapes_tunable(const Ctx &c)
+{
+    bool t = false;
+    with_fast_n(c.N, [&]<int NN>() { t = Lines<T, NN>::tuned; });
+    return t;
+}
+
+// Time the column-pass shapes of one pass on the context's spectra (9 forward and 5 inverse line
+// transforms, as in a step) and keep the fastest.  pass 0: y, 1: z.
+template <class T>
+int tune_col_pass(Ctx &c, int pass)
+{
+    const int N = c.N;
+    const int64_t h = N / 2 + 1;
+    Ptrs p{};
+    for (int i = 0; i < 9; i++) p.p[i] = reinterpret_cast<typename Cplx<T>::type *>(c.spec) + (size_t)i * c.nh;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_v = 0;
+    for (int v = 0; v < NCOLSHAPES; v++) {
+        c.col_shape[pass] = v;
+        auto run = [&]() {
+            with_fast_n(N, [&]<int NN>() {
+                using F = FastPasses<T, NN>;
+                if (pass == 0) {
+                    F::cols(c, 9, p, h, h, (int64_t)N * h, (int64_t)N * h, -1);
+                    F::cols(c, 5, p, h, h, (int64_t)N * h, (int64_t)N * h, +1);
+                } else {
+                    F::cols(c, 9, p, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, -1);
+                    F::cols(c, 5, p, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, +1);
+                }
+            });
+        };
+        run();   // warm-up (and the first launch of a new shape)
+        cudaEventRecord(e0, c.stream);
+        for (int r = 0; r < 3; r++) run();
+        cudaEventRecord(e1, c.stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.col_shape[pass] = best_v;
+    return best_v;
+}
+
+template <class T>
+bool fft_tune_shapes(Ctx &c, int force_y, int force_z)
+{
+    if (!fft_shapes_tunable<T>(c)) {
+        c.col_shape[0] = c.col_shape[1] = 0;
+        return false;
+    }
+    set_smem_attrs<T>();
+    with_fast_n(c.N, [&]<int NN>() { FastPasses<T, NN>::attrs(); });
+    if (force_y < 0 || force_z < 0) {
+        // the spectra hold nothing between steps; clear them so the timed transforms see finite data
+        cudaMemsetAsync(c.spec, 0, 9 * 2 * sizeof(T) * (size_t)c.nh, c.stream);
+    }
+    if (force_y >= 0) c.col_shape[0] = force_y;
+    else tune_col_pass<T>(c, 0);
+    if (force_z >= 0) c.col_shape[1] = force_z;
+    else tune_col_pass<T>(c, 1);
+    return true;
+}
+
+template bool fft_tune_shapes<float>(Ctx &, int, int);
+template bool fft_tune_shapes<double>(Ctx &, int, int);
 
 bool fast_fft_supported(int n)
 {

@@ -93,6 +93,7 @@ struct Ctx {
     bool newtonian = false;
     bool full_hc = false;       // PM_FULL_HC
     bool b_space = false;       // PM_B_SPACESPACE
+    int col_shape[2] = {0, 0};  // shapes of the y and z column FFT passes (pm_fft_shapes)
 
     // schedule (host, FP64)
     std::vector<double> a_n, dtau, a_half;
@@ -197,6 +198,10 @@ void launch_scan(Ctx &c);
 
 // compile-time-N FFT passes (pm_fft.cu)
 bool fast_fft_supported(int n);
+// column-pass shapes: force_* >= 0 selects one, < 0 times the choices and keeps the fastest;
+// false (shape 0 kept) when the context's precision and N have no choice
+template <class T>
+bool fft_tune_shapes(Ctx &c, int force_y, int force_z);
 void fast_twiddles(int n, std::vector<double> &re_im);
 
 }  // namespace pm

@@ -62,6 +62,7 @@ def _load():
         "pm_get_time": ([vp, C.POINTER(i32), dp, dp], C.c_int),
         "pm_get_schedule": ([vp, dp, dp, dp], C.c_int),
         "pm_get_timings": ([vp, dp, C.c_int, C.POINTER(i64)], C.c_int),
+        "pm_fft_shapes": ([vp, i32, i32, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "pm_put_particles": ([vp, vp, vp], C.c_int),
         "pm_ensemble_init": ([C.c_void_p, i32, C.POINTER(vp)], C.c_int),
         "pm_ensemble_destroy": ([vp], None),
@@ -112,7 +113,7 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_net_set_params", "pm_net_get_params", "pm_net_buffer", "pm_net_features", "pm_net_target",
             "pm_net_forward", "pm_net_backward", "pm_net_adam", "pm_net_train_step", "pm_net_apply",
             "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight",
-            "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_save", "pm_load"]
+            "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_fft_shapes", "pm_save", "pm_load"]
 
 
 def _ptr(a):
@@ -234,6 +235,14 @@ def pm_get_schedule(ctx, n_steps):
     dp = C.POINTER(C.c_double)
     _check(ctx, lib.pm_get_schedule(ctx, a.ctypes.data_as(dp), dt.ctypes.data_as(dp), ah.ctypes.data_as(dp)))
     return a, dt, ah
+
+
+def pm_fft_shapes(ctx, force_y=-1, force_z=-1):
+    """Select (0..2), keep (-2) or, with -1, time and keep the fastest y / z column-pass shape; returns the
+    shapes in use."""
+    y, z = C.c_int32(), C.c_int32()
+    _check(ctx, lib.pm_fft_shapes(ctx, force_y, force_z, C.byref(y), C.byref(z)))
+    return y.value, z.value
 
 
 def pm_get_timings(ctx):

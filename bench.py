@@ -330,12 +330,13 @@ def correction_bench(pm, torch, reps=20):
                         "BF16/FP32, He-initialised weights (timing does not depend on them)",
             "plain_step_ms": round(plain_ms, 3), "corrected_step_ms": round(corr_ms, 3),
             "forward_ms": round(fwd_ms, 3), "forward_backward_ms": round(train_ms, 3),
-            "roofline": {"bound": "tensor", "kernel": "k_conv_in2 + k_conv (4 layers)",
+            "roofline": {"bound": "tensor", "kernel": "k_conv_in2 + k_conv_tc (4 layers)",
                          "achieved": round(useful / (fwd_ms * 1e-3) / 1e12, 1), "peak": peak, "unit": "TFLOP/s",
                          "frac": round(useful / (fwd_ms * 1e-3) / 1e12 / peak, 4), "flops": useful,
                          "flops_issued": issued, "issued_tflops": round(issued / (fwd_ms * 1e-3) / 1e12, 1),
-                         "note": "algorithmic FLOPs; mma.sync m16n8k16 BF16 (legacy tensor path); of measured bf16 "
-                                 "burst peak"}}
+                         "note": "algorithmic FLOPs of measured bf16 burst peak; layers 2-4 tcgen05.mma M128 N16 K16 "
+                                 "(FP32 in TMEM), layer 1 mma.sync; with 16 output channels each MMA re-reads its "
+                                 "128x16 operand from shared memory, which bounds the kernel"}}
 
 
 def schedule_phases(pm, torch, n, n_part, box, d_pos, d_mom, stream, block=10):

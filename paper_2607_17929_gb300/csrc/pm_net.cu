@@ -10,8 +10,11 @@
 // layer's inputs and the last layer's outputs are zero-padded to 16, so every
 // layer is one 16 x 16 contraction per offset.
 //
-// Convolution as an implicit GEMM on the tensor cores (mma.sync m16n8k16,
-// BF16 in, FP32 accumulate).  One CTA computes an 8^3 tile of cells: the
+// Convolution as an implicit GEMM on the tensor cores.  Meshes with n % 16 == 0
+// take the tcgen05 kernel (k_conv_tc, below: M 128 x N 16 x K 16 MMAs from shared
+// memory into tensor memory, persistent and double-buffered); the first layer
+// (2 input channels), the weight gradient and other meshes use mma.sync
+// m16n8k16 (BF16 in, FP32 accumulate).  In k_conv one CTA computes an 8^3 tile of cells: the
 // 10^3 halo of input cells (32 B each) and the weights sit in shared memory,
 // each of the 8 warps owns one z-slice of the tile (64 cells = 4 m16 blocks
 // x 2 n8 blocks of output channels), and the K dimension runs over the 27
@@ -146,6 +149,212 @@ __global__ void __launch_bounds__(CONV_THREADS, 3)
                 }
             }
         }
+}
+
+// ---------------------------------------------------------------------------
+// The same convolution on the 5th-generation tensor cores (tcgen05.mma, BF16 in,
+// FP32 accumulate in tensor memory), for meshes with n % 16 == 0.  Persistent
+// CTAs of 128 threads walk 8 x 16 x 4 tiles of cells.  A tile's 10 x 18 x 6 halo
+// sits in shared memory in the canonical K-major layout without swizzle: the two
+// 16-byte halves of the 16 input channels in separate regions, x-rows of 16-byte
+// cells.  An M = 128 block is one z-plane of the tile (rows m = cx + 8 cy, core
+// matrices = x-rows), so the operand for offset d is the halo itself seen from a
+// shifted start address: 160 B between core matrices along M, 17280 B between the
+// channel halves.  Per tile one thread issues 4 x 27 MMAs (M 128, N 16, K 16)
+// into 64 TMEM columns and commits them to an mbarrier.  Two halo buffers and
+// two TMEM accumulators form a pipeline: while the tensor core works on tile k,
+// cp.async fetches the halo of tile k + 1 and the four warps read tile k - 1 back
+// from TMEM (tcgen05.ld), add the bias, apply ReLU and store.  The weights are
+// staged once per CTA.  Every wait is bounded: on a timeout the kernel counts it,
+// writes NaN outputs for the tile, and still frees its TMEM before returning.
+// ---------------------------------------------------------------------------
+constexpr int TCX = 8, TCY = 16, TCZ = 4;                      // tile (cells)
+constexpr int HX = TCX + 2, HY = TCY + 2, HZ = TCZ + 2;        // halo 10 x 18 x 6
+constexpr int NHT = HX * HY * HZ;                              // 1080 halo cells
+constexpr int TC_THREADS = 128;
+constexpr uint32_t HPY = HX * 16, HPZ = HY * HPY, HQ = HZ * HPZ;   // 160, 2880, 17280 bytes
+constexpr uint32_t TC_HALO = 2 * HQ;                                // one halo buffer, 34560 bytes
+constexpr uint32_t TC_A = 128, TC_B = TC_A + 2 * TC_HALO;          // shared-memory offsets
+constexpr uint32_t TC_SMEM = TC_B + NOFF * 512;                     // 83072 bytes
+constexpr uint32_t TC_COLS = 128;                                   // 2 accumulators x 4 M blocks x N 16
+// kind::f16 instruction descriptor: FP32 D (bit 4), BF16 A (bits 7-9) and B (10-12), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ unsigned int g_conv_tc_timeouts;
+
+// shared-memory matrix descriptor, no swizzle: start, leading (K) and stride (M/N) byte offsets
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// bounded wait for an mbarrier phase: each try suspends the thread for up to ~0.1 ms
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 14) && !done; it++)
+        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity), "r"(100000u));
+    return done != 0;
+}
+
+__device__ __forceinline__ void tc_tile_origin(int tile, int n, int &x0, int &y0, int &z0)
+{
+    const int ntx = n / TCX, nty = n / TCY;
+    x0 = (tile % ntx) * TCX;
+    y0 = ((tile / ntx) % nty) * TCY;
+    z0 = (tile / (ntx * nty)) * TCZ;
+}
+
+// cp.async of one tile's halo into buffer `buf`: half q of halo cell (hx, hy, hz) at q HQ + hz HPZ + hy HPY + 16 hx
+__device__ __forceinline__ void tc_load_halo(uint32_t buf, const uint4 *x, int n, int tile)
+{
+    int x0, y0, z0;
+    tc_tile_origin(tile, n, x0, y0, z0);
+    for (int i = threadIdx.x; i < 2 * NHT; i += TC_THREADS) {
+        const int h = i >> 1, q = i & 1;
+        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+        const int64_t g = ((int64_t)wrapn(z0 - 1 + hz, n) * n + wrapn(y0 - 1 + hy, n)) * n + wrapn(x0 - 1 + hx, n);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(buf + q * HQ + hz * HPZ + hy * HPY + 16 * hx),
+                     "l"(x + 2 * g + q));
+    }
+    asm volatile("cp.async.commit_group;");
+}
+
+// read the 4 M blocks of accumulator `acc` (TMEM column offset) back, add bias, activate, store
+template <bool RELU, bool OUTF32>
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, uint32_t acc, const float *bias, void *y, int n, int tile,
+                                            bool ok)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int x0, y0, z0;
+    tc_tile_origin(tile, n, x0, y0, z0);
+    // TMEM lane 32 warp + lane = M row m = cx + 8 cy of every z-plane block t (columns 16 t .. 16 t + 15)
+    const int m = 32 * warp + lane, cx = m & 7, cy = m >> 3;
+#pragma unroll 1
+    for (int t = 0; t < TCZ; t++) {
+        uint32_t r[16];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                     "[%16];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                       "=r"(r[15])
+                     : "r"(tmem + ((uint32_t)(32 * warp) << 16) + acc + 16 * t));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        float v[16];
+#pragma unroll
+        for (int c = 0; c < 16; c++) {
+            v[c] = ok ? __uint_as_float(r[c]) + (bias ? bias[c] : 0.f) : __int_as_float(0x7fc00000);
+            if (RELU) v[c] = fmaxf(v[c], 0.f);
+        }
+        const int64_t cell = ((int64_t)(z0 + t) * n + (y0 + cy)) * n + (x0 + cx);
+        if (OUTF32) {
+            float4 *o = reinterpret_cast<float4 *>(y) + 2 * cell;
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+            uint4 o[2];
+            __nv_bfloat162 *ob = reinterpret_cast<__nv_bfloat162 *>(o);
+#pragma unroll
+            for (int c = 0; c < 8; c++) ob[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+            uint4 *dst = reinterpret_cast<uint4 *>(y) + 2 * cell;
+            dst[0] = o[0];
+            dst[1] = o[1];
+        }
+    }
+}
+
+template <bool RELU, bool OUTF32>
+__global__ void __launch_bounds__(TC_THREADS)
+    k_conv_tc(const uint4 *__restrict__ x, const uint4 *__restrict__ w, const float *__restrict__ bias, void *y, int n,
+              int ntiles)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t mbar0 = sbase, tslot = sbase + 16;   // mbarriers at +0 and +8
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(TC_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // weights of offset d: half q of output channel co at TC_B + 512 d + 256 q + 16 co (once per CTA)
+    for (int i = tid; i < 2 * NOFF * CH; i += TC_THREADS) {
+        const int row = i >> 1, q = i & 1;   // row = d * 16 + co
+        *reinterpret_cast<uint4 *>(smem + TC_B + 512 * (row >> 4) + 256 * q + 16 * (row & 15)) = w[i];
+    }
+    const int first = blockIdx.x, step = gridDim.x;
+    if (first < ntiles) tc_load_halo(sbase + TC_A, x, n, first);
+    uint32_t tmem = 0;
+    bool ok = true;
+    int k = 0;
+    for (int tile = first; tile < ntiles; tile += step, k++) {
+        const int j = k & 1;
+        // 1. this tile's halo (and, the first time, the weights) visible to the tensor core
+        asm volatile("cp.async.wait_group 0;");
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        tmem = *reinterpret_cast<volatile uint32_t *>(smem + 16);
+        // 2. MMAs of this tile into accumulator j
+        if (tid == 0 && ok) {
+            // the start-address field is the low bits of a descriptor: shifted operands are the base
+            // descriptor plus a compile-time offset / 16
+            const uint64_t a0 = tc_desc(sbase + TC_A + j * TC_HALO, HQ, HPY), b0 = tc_desc(sbase + TC_B, 256, 128);
+            const uint32_t d0 = tmem + 64 * j;
+#pragma unroll
+            for (int t = 0; t < TCZ; t++)
+#pragma unroll
+                for (int d = 0; d < NOFF; d++) {
+                    const int dz = d / 9 - 1, dy = (d / 3) % 3 - 1, dx = d % 3 - 1;
+                    const uint32_t off = (t + dz + 1) * HPZ + (dy + 1) * HPY + (dx + 1) * 16;
+                    const uint64_t ad = a0 + (off >> 4), bd = b0 + 32 * d;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d0 + 16 * t),
+                                 "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(d > 0 ? 1u : 0u));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                mbar0 + 8 * j));
+        }
+        // 3. the previous tile's MMAs: its halo buffer becomes free and its accumulator readable
+        if (k > 0) {
+            if (ok && !tc_wait(mbar0 + 8 * (1 - j), ((k - 1) >> 1) & 1)) {
+                ok = false;
+                if ((tid & 31) == 0) atomicAdd(&g_conv_tc_timeouts, 1u);
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        // 4. the next tile's halo into the free buffer
+        if (tile + step < ntiles) tc_load_halo(sbase + TC_A + (1 - j) * TC_HALO, x, n, tile + step);
+        // 5. the previous tile's results
+        if (k > 0) tc_epilogue<RELU, OUTF32>(tmem, 64 * (1 - j), bias, y, n, tile - step, ok);
+    }
+    if (k > 0) {
+        const int last = first + (k - 1) * step, j = (k - 1) & 1;
+        if (ok && !tc_wait(mbar0 + 8 * j, ((k - 1) >> 1) & 1)) {
+            ok = false;
+            if ((tid & 31) == 0) atomicAdd(&g_conv_tc_timeouts, 1u);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        tc_epilogue<RELU, OUTF32>(tmem, 64 * j, bias, y, n, last, ok);
+    }
+    asm volatile("cp.async.wait_group 0;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) {
+        tmem = *reinterpret_cast<volatile uint32_t *>(smem + 16);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
+    }
 }
 
 // First layer (2 input channels): the K dimension packs 8 offsets x 2 channels per k16 step, so 27
@@ -504,18 +713,47 @@ pm_status net_fail(pm_net *e, pm_status st, const char *msg)
 
 unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// the 16-channel convolution: tensor-core (tcgen05) kernel for n % 16 == 0, mma.sync kernel otherwise
+template <bool RELU, bool OUTF32>
+void launch_conv_tc(const uint4 *x, const uint4 *w, const float *b, void *y, int n, cudaStream_t st)
+{
+    static std::atomic<uint64_t> done{0};
+    if (first_on_device(done))
+        cudaFuncSetAttribute(k_conv_tc<RELU, OUTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    const int ntiles = (n / TCX) * (n / TCY) * (n / TCZ);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(ntiles, 2 * std::max(sms, 1)));   // two resident CTAs per SM
+    k_conv_tc<RELU, OUTF32><<<grid, TC_THREADS, TC_SMEM, st>>>(x, w, b, y, n, ntiles);
+}
+
+bool conv_on_tcgen05(int n) { return n % TCY == 0; }
+
+void conv16(const uint4 *x, const uint4 *w, const float *b, void *y, int n, bool relu, bool f32, cudaStream_t st)
+{
+    if (conv_on_tcgen05(n)) {
+        if (f32) launch_conv_tc<false, true>(x, w, b, y, n, st);
+        else if (relu) launch_conv_tc<true, false>(x, w, b, y, n, st);
+        else launch_conv_tc<false, false>(x, w, b, y, n, st);
+        return;
+    }
+    const int ntiles = (n / TT) * (n / TT) * (n / TT);
+    if (f32)
+        k_conv<1, false, true><<<ntiles, CONV_THREADS, 0, st>>>(x, w, b, y, n);
+    else if (relu)
+        k_conv<2, true, false><<<ntiles, CONV_THREADS, 0, st>>>(x, w, b, y, n);
+    else
+        k_conv<2, false, false><<<ntiles, CONV_THREADS, 0, st>>>(x, w, b, y, n);
+}
+
 void conv_launch(pm_net *e, int layer, const __nv_bfloat16 *in, void *out, bool transposed, bool relu, bool f32)
 {
-    const int n = e->n, ntiles = (n / TT) * (n / TT) * (n / TT);
+    const int n = e->n;
     const uint4 *w = reinterpret_cast<const uint4 *>((transposed ? e->wt : e->wf) + (size_t)layer * WSZ);
     const float *b = transposed ? nullptr : e->bias + layer * CH;
     const uint4 *x = reinterpret_cast<const uint4 *>(in);
-    if (f32)
-        k_conv<1, false, true><<<ntiles, CONV_THREADS, 0, e->stream>>>(x, w, b, out, n);
-    else if (relu)
-        k_conv<2, true, false><<<ntiles, CONV_THREADS, 0, e->stream>>>(x, w, b, out, n);
-    else
-        k_conv<2, false, false><<<ntiles, CONV_THREADS, 0, e->stream>>>(x, w, b, out, n);
+    conv16(x, w, b, out, n, relu, f32, e->stream);
 }
 
 void net_forward(pm_net *e)
@@ -799,15 +1037,8 @@ pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float
 {
     if (!valid_net_n(n)) return PM_ERR_UNSUPPORTED_SIZE;
     if (!x || !w || !y || (c_out != 8 && c_out != 16) || (c_out == 8 && relu)) return PM_ERR_INVALID_ARG;
-    const int ntiles = (n / TT) * (n / TT) * (n / TT);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const uint4 *xx = static_cast<const uint4 *>(x), *ww = static_cast<const uint4 *>(w);
-    if (c_out == 8)
-        k_conv<1, false, true><<<ntiles, CONV_THREADS, 0, st>>>(xx, ww, bias, y, n);
-    else if (relu)
-        k_conv<2, true, false><<<ntiles, CONV_THREADS, 0, st>>>(xx, ww, bias, y, n);
-    else
-        k_conv<2, false, false><<<ntiles, CONV_THREADS, 0, st>>>(xx, ww, bias, y, n);
+    conv16(static_cast<const uint4 *>(x), static_cast<const uint4 *>(w), bias, y, n, relu != 0, c_out == 8, st);
     return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
 }
 

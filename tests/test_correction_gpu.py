@@ -49,8 +49,9 @@ def uncl(y, c, n):
     return np.ascontiguousarray(y[:, :c].T).reshape(c, n, n, n)
 
 
-@pytest.mark.parametrize("n,relu", [(8, True), (16, False), (24, True)])
+@pytest.mark.parametrize("n,relu", [(8, True), (16, False), (24, True), (32, True), (48, False)])
 def test_conv_forward_bf16_matches_oracle(env, n, relu):
+    """Meshes with n % 16 == 0 run the tcgen05 kernel (8 x 16 x 4 cell tiles), the others the mma.sync one."""
     torch, pm = env
     rng = np.random.default_rng(n)
     x_t, x = bf16(torch, cl(rng.standard_normal((16, n, n, n))))
@@ -67,9 +68,9 @@ def test_conv_forward_bf16_matches_oracle(env, n, relu):
     assert np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.sqrt(np.mean(ref ** 2))), err.max()
 
 
-def test_conv_forward_fp32_output_matches_oracle(env):
+@pytest.mark.parametrize("n", [16, 24])
+def test_conv_forward_fp32_output_matches_oracle(env, n):
     torch, pm = env
-    n = 16
     rng = np.random.default_rng(7)
     x_t, x = bf16(torch, cl(rng.standard_normal((16, n, n, n))))
     w_t, w = bf16(torch, 0.1 * rng.standard_normal((27, 16, 16)))

@@ -339,6 +339,26 @@ def correction_bench(pm, torch, reps=20):
                                  "128x16 operand from shared memory, which bounds the kernel"}}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over the ranks (the job's time is its slowest rank's); x itself on one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms_max):
+    """Units processed by all ranks per second, timed by the slowest rank (weak scaling: each rank its own box)."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
+def replica_seed(rank):
+    """Seed of a rank's replica: every rank steps its own box."""
+    return SEED + rank
+
+
 def schedule_phases(pm, torch, n, n_part, box, d_pos, d_mom, stream, block=10):
     """The whole 100-step schedule (z = 100 -> 0) in blocks of `block` steps, each timed with CUDA events
     with its per-kernel means: clustering makes late steps costlier for the deposit and the sort."""
@@ -542,12 +562,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x):
+        return max_over_ranks(x, dist, "cuda")
 
     # inputs: the same seeded initial conditions for every rank's replica (seed offset per rank)
     probe = pm.PM(8, 8, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED)
@@ -555,7 +571,7 @@ def main():
     probe.close()
     a_m = half_step_back(a_n[0], dtau[0], box)
     t_ic = time.perf_counter()
-    pos, mom = make_ics(n, box, SEED + rank, a_n[0], a_m)
+    pos, mom = make_ics(n, box, replica_seed(rank), a_n[0], a_m)
     t_ic = time.perf_counter() - t_ic
     d_pos = torch.from_numpy(pos).cuda()
     d_mom = torch.from_numpy(mom).cuda()
@@ -582,8 +598,8 @@ def main():
         return sim, ms, per_kernel, launches, clk.summary()
 
     sim, ms_mixed, kern, launches, clocks = timed_run(pm.PM_MIXED, args.warmup, args.steps)
-    ms_max = max_over_ranks(ms_mixed)
-    value = world * n_part / (ms_max * 1e-3)
+    ms_max = max_ranks(ms_mixed)
+    value = whole_job_rate(world, n_part, ms_max)
 
     # end to end through the C ABI with pinned host buffers: upload the state, step, read it back
     h_pos = torch.from_numpy(pos).pin_memory()
@@ -602,7 +618,7 @@ def main():
         pm.pm_get_particles(sim.ctx, o_pos, o_mom)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.e2e_steps)
+    e2e_ms = max_ranks(1e3 * (time.perf_counter() - t0) / args.e2e_steps)
     sim.close()
     del sim
 
@@ -617,7 +633,7 @@ def main():
     if not args.no_fp64:
         sim64, ms64, kern64, _, _ = timed_run(pm.PM_FP64, 2, args.fp64_steps)
         sim64.close()
-        ms64 = max_over_ranks(ms64)
+        ms64 = max_ranks(ms64)
         fp64 = {"ms_per_step": ms64, "value": world * n_part / (ms64 * 1e-3),
                 "speedup_mixed_over_fp64": ms64 / ms_max,
                 "kernels_ms": {k: round(v, 4) for k, v in kern64.items()},
@@ -635,7 +651,7 @@ def main():
             simv, msv, kernv, _, _ = timed_run(pm.PM_MIXED, 3, args.variant_steps, flags)
             simv.close()
             del simv
-            msv = max_over_ranks(msv)
+            msv = max_ranks(msv)
             variants[name] = {"ms_per_step": round(msv, 3), "value": world * n_part / (msv * 1e-3),
                               "kernels_ms": {k: round(v, 4) for k, v in kernv.items()}}
         torch.cuda.empty_cache()

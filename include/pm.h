@@ -374,6 +374,12 @@ pm_status pm_set_correction(pm_ctx *ctx, const float *corr);
  * with w'[26 - d][c_in][c_out] = w[d][c_out][c_in]. */
 pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float *bias, int32_t c_out, int32_t relu,
                             void *y, void *stream);
+/* Synchronise `stream` and report whether a bounded device wait of the
+ * tensor-core convolution (meshes with n % 16 == 0, in pm_conv3d_forward and
+ * in the network calls) ran out since the previous check: PM_ERR_TIMEOUT
+ * (the count is then cleared; the affected outputs hold NaN and the
+ * context stays usable), else PM_OK.  The count is per device.  Errors: CUDA. */
+pm_status pm_conv3d_check(void *stream);
 /* dw[d][c_out][c_in] += sum over cells of g[cell][c_out] x[cell + d][c_in]
  * (x, g BF16 [n^3][16]; dw FP32 [27][16][16], accumulated with atomics). */
 pm_status pm_conv3d_backward_weight(int32_t n, const void *x, const void *g, float *dw, void *stream);

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -271,7 +272,7 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, uint32_t acc, const f
 template <bool RELU, bool OUTF32>
 __global__ void __launch_bounds__(TC_THREADS)
     k_conv_tc(const uint4 *__restrict__ x, const uint4 *__restrict__ w, const float *__restrict__ bias, void *y, int n,
-              int ntiles)
+              int ntiles, int skip_mma)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS)
         asm volatile("tcgen05.fence::after_thread_sync;");
         tmem = *reinterpret_cast<volatile uint32_t *>(smem + 16);
         // 2. MMAs of this tile into accumulator j
-        if (tid == 0 && ok) {
+        if (tid == 0 && ok && !skip_mma) {
             // the start-address field is the low bits of a descriptor: shifted operands are the base
             // descriptor plus a compile-time offset / 16
             const uint64_t a0 = tc_desc(sbase + TC_A + j * TC_HALO, HQ, HPY), b0 = tc_desc(sbase + TC_B, 256, 128);
@@ -725,7 +726,10 @@ void launch_conv_tc(const uint4 *x, const uint4 *w, const float *b, void *y, int
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(ntiles, 2 * std::max(sms, 1)));   // two resident CTAs per SM
-    k_conv_tc<RELU, OUTF32><<<grid, TC_THREADS, TC_SMEM, st>>>(x, w, b, y, n, ntiles);
+    // PM_TEST_CONV_TIMEOUT=1 (test hook): no MMA is issued, so every bounded wait runs out
+    const char *inj = std::getenv("PM_TEST_CONV_TIMEOUT");
+    const int skip = inj && std::atoi(inj) != 0;
+    k_conv_tc<RELU, OUTF32><<<grid, TC_THREADS, TC_SMEM, st>>>(x, w, b, y, n, ntiles, skip);
 }
 
 bool conv_on_tcgen05(int n) { return n % TCY == 0; }
@@ -1040,6 +1044,22 @@ pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     conv16(static_cast<const uint4 *>(x), static_cast<const uint4 *>(w), bias, y, n, relu != 0, c_out == 8, st);
     return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+}
+
+pm_status pm_conv3d_check(void *stream)
+{
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize();
+    unsigned int t = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&t, g_conv_tc_timeouts, sizeof(t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ERR_CUDA;
+    }
+    if (t == 0) return PM_OK;
+    const unsigned int zero = 0;
+    cudaMemcpyToSymbol(g_conv_tc_timeouts, &zero, sizeof(zero));
+    return PM_ERR_TIMEOUT;
 }
 
 pm_status pm_conv3d_backward_weight(int32_t n, const void *x, const void *g, float *dw, void *stream)

@@ -93,6 +93,7 @@ def _load():
         "pm_net_set_scales": ([vp, C.c_double, C.c_double, C.c_double], C.c_int),
         "pm_conv3d_forward": ([i32, vp, vp, vp, i32, i32, vp, vp], C.c_int),
         "pm_conv3d_backward_weight": ([i32, vp, vp, vp, vp], C.c_int),
+        "pm_conv3d_check": ([vp], C.c_int),
         "pm_save": ([vp, C.c_char_p], C.c_int),
         "pm_load": ([vp, C.c_char_p], C.c_int),
     }
@@ -112,7 +113,7 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_ensemble_stream", "pm_ensemble_set_streams", "pm_net_param_count", "pm_net_create", "pm_net_destroy", "pm_net_last_error",
             "pm_net_set_params", "pm_net_get_params", "pm_net_buffer", "pm_net_features", "pm_net_target",
             "pm_net_forward", "pm_net_backward", "pm_net_adam", "pm_net_train_step", "pm_net_apply",
-            "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight",
+            "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight", "pm_conv3d_check",
             "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_fft_shapes", "pm_save", "pm_load"]
 
 
@@ -418,6 +419,13 @@ def pm_conv3d_backward_weight(n, x, g, dw, stream=None):
     st = lib.pm_conv3d_backward_weight(int(n), _ptr(x), _ptr(g), _ptr(dw), _stream(stream))
     if st != PM_OK:
         raise PMError(st, "pm_conv3d_backward_weight failed")
+
+
+def pm_conv3d_check(stream=None):
+    """Raise PMError(PM_ERR_TIMEOUT) if a bounded wait of the tensor-core convolution ran out since the last check."""
+    st = lib.pm_conv3d_check(_stream(stream))
+    if st != PM_OK:
+        raise PMError(st, "pm_conv3d_check: " + STATUS_NAMES.get(st, str(st)))
 
 
 class PM:

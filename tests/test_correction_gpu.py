@@ -314,3 +314,31 @@ def test_training_driver_end_to_end_small(env):
     for name in ("plain", "corrected"):
         assert np.isfinite(res[name]["rms_displacement_error_cells"])
     pm.pm_net_destroy(net)
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_context_stays_usable(env):
+    """PM_TEST_CONV_TIMEOUT=1 makes the tcgen05 convolution issue no MMA, so its bounded waits run out:
+    pm_conv3d_check reports PM_ERR_TIMEOUT, the outputs are NaN, and the next convolution is correct."""
+    import os
+    torch, pm = env
+    n = 16
+    rng = np.random.default_rng(23)
+    x_t, x = bf16(torch, cl(rng.standard_normal((16, n, n, n))))
+    w_t, w = bf16(torch, 0.1 * rng.standard_normal((27, 16, 16)))
+    b = torch.zeros(16, dtype=torch.float32, device="cuda")
+    y = torch.empty((n ** 3, 16), dtype=torch.bfloat16, device="cuda")
+    pm.pm_conv3d_check()   # clear any earlier count
+    os.environ["PM_TEST_CONV_TIMEOUT"] = "1"
+    try:
+        pm.pm_conv3d_forward(n, x_t, w_t, b, 16, 0, y)
+        with pytest.raises(pm.PMError) as ei:
+            pm.pm_conv3d_check()
+        assert ei.value.status == pm.PM_ERR_TIMEOUT
+        assert torch.isnan(y.float()).all()
+    finally:
+        del os.environ["PM_TEST_CONV_TIMEOUT"]
+    pm.pm_conv3d_forward(n, x_t, w_t, b, 16, 0, y)
+    pm.pm_conv3d_check()
+    ref = NC.conv(uncl(x, 16, n), w, np.zeros(16))
+    got = uncl(y.float().cpu().numpy().astype(np.float64), 16, n)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.sqrt(np.mean(ref ** 2)))

@@ -133,7 +133,8 @@ __device__ __forceinline__ T hc_remainder(const T *sphi, const T *schi, int vo, 
            T(1.5) * (p.hc * p.hc * expm1_minus_x(x) - T(2) * p.hc * dphi * em + dphi * dphi * (em + T(1)));
 }
 
-template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 1024; }
+// particle records per shared-memory chunk: 960 (FP32) was the fastest of 640-1024 at 512^3, early and late
+template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 960; }
 
 template <class T> size_t dep_smem()
 {

@@ -121,6 +121,26 @@ def test_fp64_clustered_tile_needs_several_chunks(pm):
     assert all(v < 1e-11 for v in e.values()), e
 
 
+def test_mixed_clustered_tile_needs_several_chunks(pm):
+    """The mixed form on the clustered load above (5000 particles in 2^3 cells: one tile takes several
+    960-particle chunks) against the FP64 oracle, with the mixed bounds of the 32^3 test."""
+    n = 16
+    rng = np.random.default_rng(3)
+    pos = np.concatenate([(5.0 + 2.0 * rng.random((5000, 3))) / n, rng.random((2000, 3))])
+    mom = rng.standard_normal(pos.shape) * 1e-4
+    orc, g, *_ = make_pair(pm, n, 0, 160.0, 0, pm.PM_MIXED, pos=pos, mom=mom)
+    worst = {}
+    for _ in range(2):
+        orc.step()
+        g.step()
+        for k, v in compare(orc, g, n).items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    g.close()
+    assert worst["phi"] < 1e-5 and worst["R"] < 1e-5 and worst["u"] < 1e-5, worst
+    for k in ("chi", "B", "Fx", "Sxx", "h+", "hx"):
+        assert worst[k] < 1e-3, (k, worst[k])
+
+
 def test_fp64_newtonian_zero_net_momentum(pm):
     n = 32
     orc, g, pos, mom = make_pair(pm, n, n, 320.0, 2, pm.PM_FP64, newtonian=True)

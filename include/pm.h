@@ -371,7 +371,12 @@ pm_status pm_set_correction(pm_ctx *ctx, const float *corr);
  * ([d][c_out][c_in]), bias FP32 [16] or NULL; c_out = 16 writes BF16
  * [n^3][16] (relu 0/1), c_out = 8 writes FP32 [n^3][8] (relu 0) from the first
  * 8 output channels of w.  The input gradient of a layer is this convolution
- * with w'[26 - d][c_in][c_out] = w[d][c_out][c_in]. */
+ * with w'[26 - d][c_in][c_out] = w[d][c_out][c_in].  Meshes with n % 16 == 0
+ * run on the tcgen05 tensor cores (FP32 accumulate in tensor memory), others
+ * on mma.sync; both accumulate in FP32 over the 27 offsets in order.
+ * Errors: UNSUPPORTED_SIZE (n not a multiple of 8 in 8..1024), INVALID_ARG,
+ * CUDA (launch); a device-side wait that runs out is reported by
+ * pm_conv3d_check. */
 pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float *bias, int32_t c_out, int32_t relu,
                             void *y, void *stream);
 /* Synchronise `stream` and report whether a bounded device wait of the

@@ -339,6 +339,21 @@ def correction_bench(pm, torch, reps=20):
                                  "128x16 operand from shared memory, which bounds the kernel"}}
 
 
+def host_cpu():
+    """CPU model and logical core count of this host (recorded beside the CPU baseline)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and not model:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def max_over_ranks(x, dist=None, device="cpu"):
     """The largest value of x over the ranks (the job's time is its slowest rank's); x itself on one rank."""
     if dist is None:
@@ -510,7 +525,7 @@ def run_reference(args):
         "dtype": "f64", "data": "synthetic",
         "config": workload_config(args.n, CELL_MPCH * args.n, args.warmup, args.steps, args.gpus),
         "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": sample + "; the FP64 CPU oracle, single thread"},
+                         "sample": sample + "; the FP64 CPU oracle, single thread", "host": host_cpu()},
         "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -694,7 +709,7 @@ def main():
         rate, dt = cpu_oracle_rate(nc_, 2, CELL_MPCH * nc_)
         cpu = {"value": rate, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"2 steps of the same recipe at {nc_}^3 (box {CELL_MPCH * nc_:.0f} Mpc/h, same cell "
-                         f"size) after its bootstrap, single thread, {dt:.1f} s"}
+                         f"size) after its bootstrap, single thread, {dt:.1f} s", "host": host_cpu()}
 
     if rank == 0:
         h2d = 2 * 3 * 8 * n_part

@@ -341,16 +341,23 @@ def correction_bench(pm, torch, reps=20):
 
 def host_cpu():
     """CPU model and logical core count of this host (recorded beside the CPU baseline)."""
-    model = ""
+    model, arm = "", {}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                key = line.split(":")[0].strip().lower()
+                if ":" not in line:
+                    continue
+                key, val = (x.strip() for x in line.split(":", 1))
+                key = key.lower()
                 if key in ("model name", "cpu model", "hardware") and not model:
-                    model = line.split(":", 1)[1].strip()
+                    model = val
+                elif key in ("cpu implementer", "cpu part") and key not in arm:
+                    arm[key] = val
     except OSError:
         pass
     import platform
+    if not model and arm:   # Arm cores name themselves by implementer and part number (0x41 0xd4f: Neoverse V2)
+        model = f"{platform.machine()} implementer {arm.get('cpu implementer', '?')} part {arm.get('cpu part', '?')}"
     return {"model": model or platform.machine(), "nproc": os.cpu_count()}
 
 

@@ -191,6 +191,85 @@ def test_projection_ultrarelativistic_equation_of_state():
     assert rel(trace, s00) <= 1e-4
 
 
+def _unexpanded_stress(a, m, u, phi, chi):
+    """Eqs. (matterstress) for one particle without expansion, scaled to the projected quantities.
+
+    q = m u, alpha = a e^psi with psi = phi - chi, gamma^ij = a^-2 e^{2 phi} delta^ij,
+    sqrt(gamma) = a^3 e^{-3 phi}.  Returns the per-particle weights of
+    4piG a^4 e^{2psi} T^00 / (4piG a^-2), 4piG a^2 e^{2psi} T^0_i / (4piG a^-2) and a^2 T_ij,
+    which is what the projection deposits as S00, S0i and Sij.
+    """
+    psi = phi - chi
+    q = m * np.asarray(u, dtype=np.float64)
+    alpha = a * math.exp(psi)
+    sqrt_gamma = a ** 3 * math.exp(-3.0 * phi)
+    g_up = math.exp(2.0 * phi) / a ** 2
+    root = math.sqrt(m * m + g_up * (q @ q))
+    t00 = root / (alpha ** 2 * sqrt_gamma)
+    t0i = q / (alpha * sqrt_gamma)
+    tij = np.outer(q, q) / (sqrt_gamma * root)
+    s00 = a ** 4 * math.exp(2.0 * psi) * t00 * a ** 2
+    s0i = a ** 2 * math.exp(2.0 * psi) * t0i * a ** 2
+    sij = a ** 2 * tij
+    return s00, s0i, sij
+
+
+def _expanded_stress_planted(a, m, u, phi, chi, flip):
+    """The first-order projection weights with one phi u^2/E^2 sign flipped (a planted mistake)."""
+    u = np.asarray(u, dtype=np.float64)
+    u2 = u @ u
+    E = math.sqrt(a * a + u2)
+    s00 = m * E * (1 + 3 * phi + (-1 if flip == "s00" else 1) * phi * u2 / E ** 2)
+    s0i = m * u * (1 + 4 * phi - chi)
+    sij = m * np.outer(u, u) * (1 + 3 * phi + (1 if flip == "sij" else -1) * phi * u2 / E ** 2) / E
+    return s00, s0i, sij
+
+
+def test_projection_matches_unexpanded_stress_energy_to_second_order():
+    """Eqs. (matterstress) expanded to first order in phi, psi: fast particles (u/E = 0.3-0.9) in uniform
+    potentials carry the phi u^2/E^2 cross terms of S00 and Sij and the (1 + 4 phi - chi) factor of S0i.  The
+    difference to the unexpanded expressions must be quadratic in the amplitude: it quarters when the amplitude
+    halves.  The same criterion, applied to the expansion with either phi u^2/E^2 sign flipped, fails."""
+    n, a = 8, 0.05
+    m = 0.31 / 5
+    rng = np.random.default_rng(21)
+    pos = rng.random((5, 3))
+    # momenta with u/E spread over 0.3 .. 0.9
+    frac = np.array([0.3, 0.45, 0.6, 0.75, 0.9])
+    dirs = rng.standard_normal((5, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    mom = dirs * (a * frac / np.sqrt(1 - frac ** 2))[:, None]
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+    def errors(amp, model):
+        phi, chi = amp, -0.7 * amp   # psi = 1.7 amp
+        e00 = e0i = eij = 0.0
+        for k in range(len(pos)):
+            ex00, ex0i, exij = _unexpanded_stress(a, m, mom[k], phi, chi)
+            if model is None:
+                s00, s0i, sij = O.project(n, pos[k:k + 1], mom[k:k + 1], m, a, np.full((n, n, n), phi),
+                                          np.full((n, n, n), chi))
+                got00 = s00.sum() / n ** 3
+                got0i = s0i.reshape(3, -1).sum(1) / n ** 3
+                gotij = np.array([[sij[pairs.index((min(i, j), max(i, j)))].sum() / n ** 3 for j in range(3)]
+                                  for i in range(3)])
+            else:
+                got00, got0i, gotij = _expanded_stress_planted(a, m, mom[k], phi, chi, model)
+            e00 = max(e00, abs(got00 - ex00) / abs(ex00))
+            e0i = max(e0i, np.max(np.abs(got0i - ex0i)) / np.max(np.abs(ex0i)))
+            eij = max(eij, np.max(np.abs(gotij - exij)) / np.max(np.abs(exij)))
+        return np.array([e00, e0i, eij])
+
+    big, small = errors(2e-3, None), errors(1e-3, None)
+    ratio = big / small
+    assert np.all((3.6 < ratio) & (ratio < 4.4)), ratio
+    assert np.all(big < 40 * 2e-3 ** 2), big
+    # the pin separates: with a flipped cross term the error is first order (ratio 2)
+    for flip, comp in (("s00", 0), ("sij", 2)):
+        r = errors(2e-3, flip) / errors(1e-3, flip)
+        assert not (3.6 < r[comp] < 4.4), (flip, r)
+
+
 # ------------------------------------------------------------- solves -------
 
 def test_single_mode_phi_closed_form():

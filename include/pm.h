@@ -206,10 +206,13 @@ pm_status pm_power_spectrum(pm_ctx *ctx, int nbins, double *k, double *pk, int64
  * Memory: all scratch (density, spectrum, bins, twiddle tables, about 4.3 MiB)
  * is one file-scope __device__ array that every GPU loading the library holds
  * until the process exits.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) and should come before any stream
- * capture.  Every call uses the same array, so calls that overlap on the GPU
- * (on different streams or host threads) race and must be serialised by the
- * caller.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA. */
+ * device address (cudaGetSymbolAddress).  Every call ends by copying the bins to
+ * the host and synchronising `stream`, so it cannot be recorded into a CUDA
+ * graph: inside a stream capture it fails with PM_ERR_CUDA.  Every call uses the
+ * same array, so calls that overlap on the GPU (on different streams or host
+ * threads) race and must be serialised by the caller.  Device memory of another
+ * GPU than the current one is rejected with INVALID_ARG.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA. */
 pm_status pm_power_spectrum_noalloc(const double *d_pos, int64_t n_part, int32_t n_mesh, double omega_m,
                                     int32_t nbins, double *k, double *pk, int64_t *nmodes, void *stream);
 
@@ -382,8 +385,14 @@ pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float
 /* Synchronise `stream` and report whether a bounded device wait of the
  * tensor-core convolution (meshes with n % 16 == 0, in pm_conv3d_forward and
  * in the network calls) ran out since the previous check: PM_ERR_TIMEOUT
- * (the count is then cleared; the affected outputs hold NaN and the
- * context stays usable), else PM_OK.  The count is per device.  Errors: CUDA. */
+ * (the count is then cleared; the affected outputs hold NaN), else PM_OK.
+ * The count is per device.  After a timeout a CTA issues no further work and
+ * waits once more, bounded, for the MMAs it committed before it frees its
+ * tensor memory.  If that second wait also runs out, the convolutions are
+ * poisoned for the rest of the process: this call and every later
+ * pm_conv3d_forward, pm_net_forward and pm_net_backward return PM_ERR_STATE.
+ * Only the timeout in which no MMA was issued is exercised by the tests (it
+ * leaves the calls usable).  Errors: CUDA. */
 pm_status pm_conv3d_check(void *stream);
 /* dw[d][c_out][c_in] += sum over cells of g[cell][c_out] x[cell + d][c_in]
  * (x, g BF16 [n^3][16]; dw FP32 [27][16][16], accumulated with atomics). */

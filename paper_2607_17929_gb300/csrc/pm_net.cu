@@ -166,8 +166,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 3)
 // two TMEM accumulators form a pipeline: while the tensor core works on tile k,
 // cp.async fetches the halo of tile k + 1 and the four warps read tile k - 1 back
 // from TMEM (tcgen05.ld), add the bias, apply ReLU and store.  The weights are
-// staged once per CTA.  Every wait is bounded: on a timeout the kernel counts it,
-// writes NaN outputs for the tile, and still frees its TMEM before returning.
+// staged once per CTA.  Every wait is bounded.  On a timeout the CTA agrees on the
+// failure at its next barrier, issues no further MMAs or halo loads, writes NaN
+// outputs, and before freeing its TMEM waits once more (bounded) for every MMA
+// batch it committed and has not seen complete; a batch still pending after that
+// is counted as an unsafe exit, which poisons the convolution entry points.
 // ---------------------------------------------------------------------------
 constexpr int TCX = 8, TCY = 16, TCZ = 4;                      // tile (cells)
 constexpr int HX = TCX + 2, HY = TCY + 2, HZ = TCZ + 2;        // halo 10 x 18 x 6
@@ -183,6 +186,7 @@ constexpr uint32_t TC_COLS = 128;                                   // 2 accumul
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ unsigned int g_conv_tc_timeouts;
+__device__ unsigned int g_conv_tc_unsafe;   // CTAs that freed TMEM with an MMA batch possibly in flight
 
 // shared-memory matrix descriptor, no swizzle: start, leading (K) and stride (M/N) byte offsets
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
@@ -238,14 +242,16 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, uint32_t acc, const f
     const int m = 32 * warp + lane, cx = m & 7, cy = m >> 3;
 #pragma unroll 1
     for (int t = 0; t < TCZ; t++) {
-        uint32_t r[16];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                     "[%16];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                       "=r"(r[15])
-                     : "r"(tmem + ((uint32_t)(32 * warp) << 16) + acc + 16 * t));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        uint32_t r[16] = {};
+        if (ok) {   // warp-uniform: after a timeout the accumulator is not read
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                         "[%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(tmem + ((uint32_t)(32 * warp) << 16) + acc + 16 * t));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+        }
         float v[16];
 #pragma unroll
         for (int c = 0; c < 16; c++) {
@@ -296,17 +302,25 @@ __global__ void __launch_bounds__(TC_THREADS)
     if (first < ntiles) tc_load_halo(sbase + TC_A, x, n, first);
     uint32_t tmem = 0;
     bool ok = true;
+    // MMA batches committed to mbarrier 0 / 1 and the waits on them that completed (all threads count the
+    // commits alike, since ok is CTA-uniform where they are issued)
+    int iss0 = 0, iss1 = 0, fin0 = 0, fin1 = 0;
     int k = 0;
     for (int tile = first; tile < ntiles; tile += step, k++) {
         const int j = k & 1;
-        // 1. this tile's halo (and, the first time, the weights) visible to the tensor core
+        // 1. this tile's halo (and, the first time, the weights) visible to the tensor core; the CTA agrees
+        //    on whether any wait has timed out
         asm volatile("cp.async.wait_group 0;");
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        ok = __syncthreads_and(ok) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;");
         tmem = *reinterpret_cast<volatile uint32_t *>(smem + 16);
         // 2. MMAs of this tile into accumulator j
+        if (ok && !skip_mma) {
+            if (j) iss1++;
+            else iss0++;
+        }
         if (tid == 0 && ok && !skip_mma) {
             // the start-address field is the low bits of a descriptor: shifted operands are the base
             // descriptor plus a compile-time offset / 16
@@ -327,32 +341,53 @@ __global__ void __launch_bounds__(TC_THREADS)
                 mbar0 + 8 * j));
         }
         // 3. the previous tile's MMAs: its halo buffer becomes free and its accumulator readable
-        if (k > 0) {
-            if (ok && !tc_wait(mbar0 + 8 * (1 - j), ((k - 1) >> 1) & 1)) {
+        if (k > 0 && ok) {
+            if (tc_wait(mbar0 + 8 * (1 - j), ((k - 1) >> 1) & 1)) {
+                if (j) fin0++;
+                else fin1++;
+            } else {
                 ok = false;
                 if ((tid & 31) == 0) atomicAdd(&g_conv_tc_timeouts, 1u);
             }
+            ok = __all_sync(0xffffffffu, ok) != 0;   // warp-uniform for the TMEM reads
             asm volatile("tcgen05.fence::after_thread_sync;");
         }
-        // 4. the next tile's halo into the free buffer
-        if (tile + step < ntiles) tc_load_halo(sbase + TC_A + (1 - j) * TC_HALO, x, n, tile + step);
+        // 4. the next tile's halo into the free buffer (none after a timeout: the buffer may still be read)
+        if (ok && tile + step < ntiles) tc_load_halo(sbase + TC_A + (1 - j) * TC_HALO, x, n, tile + step);
         // 5. the previous tile's results
         if (k > 0) tc_epilogue<RELU, OUTF32>(tmem, 64 * (1 - j), bias, y, n, tile - step, ok);
     }
     if (k > 0) {
         const int last = first + (k - 1) * step, j = (k - 1) & 1;
-        if (ok && !tc_wait(mbar0 + 8 * j, ((k - 1) >> 1) & 1)) {
-            ok = false;
-            if ((tid & 31) == 0) atomicAdd(&g_conv_tc_timeouts, 1u);
+        if (ok) {
+            if (tc_wait(mbar0 + 8 * j, ((k - 1) >> 1) & 1)) {
+                if (j) fin1++;
+                else fin0++;
+            } else {
+                ok = false;
+                if ((tid & 31) == 0) atomicAdd(&g_conv_tc_timeouts, 1u);
+            }
+            ok = __all_sync(0xffffffffu, ok) != 0;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         tc_epilogue<RELU, OUTF32>(tmem, 64 * j, bias, y, n, last, ok);
     }
     asm volatile("cp.async.wait_group 0;");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) {
+        if (!ok) {
+            // drain: at most one batch per mbarrier is outstanding (a batch is committed only after the wait on
+            // the previous batch of the same mbarrier completed); its phase parity is the completed count's.
+            // Re-waiting a phase this thread gave up on but that completed since returns at once.
+            bool drained = true;
+            if (iss0 > fin0) drained = tc_wait(mbar0, fin0 & 1) && drained;
+            if (iss1 > fin1) drained = tc_wait(mbar0 + 8, fin1 & 1) && drained;
+            if (!drained) atomicAdd(&g_conv_tc_unsafe, 1u);
+            __syncwarp();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
         tmem = *reinterpret_cast<volatile uint32_t *>(smem + 16);
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
     }
@@ -706,6 +741,10 @@ struct pm_net {
 
 namespace {
 
+// set once a CTA of the tensor-core convolution had to free its TMEM while an MMA batch it committed may still
+// have been running (a wait ran out twice): every later convolution call returns PM_ERR_STATE
+std::atomic<bool> g_conv_poisoned{false};
+
 pm_status net_fail(pm_net *e, pm_status st, const char *msg)
 {
     e->err = msg;
@@ -899,6 +938,7 @@ pm_status pm_net_buffer(pm_net *e, int32_t which, void **ptr)
 pm_status pm_net_forward(pm_net *e)
 {
     if (!e) return PM_ERR_INVALID_ARG;
+    if (g_conv_poisoned.load()) return net_fail(e, PM_ERR_STATE, "pm_net_forward: convolutions poisoned");
     net_forward(e);
     return cudaGetLastError() == cudaSuccess ? PM_OK : net_fail(e, PM_ERR_CUDA, "pm_net_forward: launch failed");
 }
@@ -906,6 +946,7 @@ pm_status pm_net_forward(pm_net *e)
 pm_status pm_net_backward(pm_net *e, const float *target, double *loss)
 {
     if (!e || !target) return PM_ERR_INVALID_ARG;
+    if (g_conv_poisoned.load()) return net_fail(e, PM_ERR_STATE, "pm_net_backward: convolutions poisoned");
     const int64_t nc = e->ncell;
     const int n = e->n;
     net_forward(e);
@@ -1039,6 +1080,7 @@ pm_status pm_set_correction(pm_ctx *ctx, const float *corr)
 pm_status pm_conv3d_forward(int32_t n, const void *x, const void *w, const float *bias, int32_t c_out, int32_t relu,
                             void *y, void *stream)
 {
+    if (g_conv_poisoned.load()) return PM_ERR_STATE;
     if (!valid_net_n(n)) return PM_ERR_UNSUPPORTED_SIZE;
     if (!x || !w || !y || (c_out != 8 && c_out != 16) || (c_out == 8 && relu)) return PM_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1050,13 +1092,15 @@ pm_status pm_conv3d_check(void *stream)
 {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize();
-    unsigned int t = 0;
+    unsigned int t = 0, u = 0;
     if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&t, g_conv_tc_timeouts, sizeof(t));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&u, g_conv_tc_unsafe, sizeof(u));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return PM_ERR_CUDA;
     }
-    if (t == 0) return PM_OK;
+    if (u != 0) g_conv_poisoned.store(true);   // TMEM was freed with MMAs possibly in flight
+    if (t == 0) return g_conv_poisoned.load() ? PM_ERR_STATE : PM_OK;
     const unsigned int zero = 0;
     cudaMemcpyToSymbol(g_conv_tc_timeouts, &zero, sizeof(zero));
     return PM_ERR_TIMEOUT;

@@ -121,7 +121,8 @@ extern "C" pm_status pm_power_spectrum_noalloc(const double *d_pos, int64_t n_pa
     }
     cudaPointerAttributes attr{};
     if (cudaPointerGetAttributes(&attr, d_pos) != cudaSuccess ||
-        !(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged)) {
+        !(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) ||
+        (attr.type == cudaMemoryTypeDevice && attr.device != dev)) {
         cudaGetLastError();
         return PM_ERR_INVALID_ARG;
     }

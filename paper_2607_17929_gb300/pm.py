@@ -212,9 +212,26 @@ def pm_power_spectrum(ctx, nbins):
 
 
 def pm_power_spectrum_noalloc(d_pos, n_mesh, omega_m, nbins, stream=None):
-    """P(k) of device positions without any device allocation (see include/pm.h for who needs it)."""
+    """P(k) of device positions without any device allocation (see include/pm.h for who needs it).
+
+    d_pos must be an (n, 3) float64 CUDA tensor on the current device (or an (n, 3) float64 numpy array, which
+    the library rejects as host memory).  Anything else raises ValueError before the library is called: the
+    kernels read 3 * n doubles from the pointer, so a flat or FP32 array would be read past its end.
+    """
+    shape = tuple(getattr(d_pos, "shape", ()))
+    if len(shape) != 2 or shape[1] != 3 or shape[0] < 1:
+        raise ValueError(f"pm_power_spectrum_noalloc: positions must have shape (n, 3), got {shape}")
+    if isinstance(d_pos, np.ndarray):
+        if d_pos.dtype != np.float64 or not d_pos.flags["C_CONTIGUOUS"]:
+            raise ValueError("pm_power_spectrum_noalloc: positions must be C-contiguous float64")
+    else:
+        import torch
+        if not isinstance(d_pos, torch.Tensor) or d_pos.dtype != torch.float64 or not d_pos.is_contiguous():
+            raise ValueError("pm_power_spectrum_noalloc: positions must be a contiguous float64 tensor")
+        if not d_pos.is_cuda or d_pos.device.index != torch.cuda.current_device():
+            raise ValueError("pm_power_spectrum_noalloc: positions must live on the current CUDA device")
     k = np.zeros(nbins); pk = np.zeros(nbins); nm = np.zeros(nbins, dtype=np.int64)
-    n_part = d_pos.shape[0] if hasattr(d_pos, "shape") else len(d_pos) // 3
+    n_part = shape[0]
     st = lib.pm_power_spectrum_noalloc(_ptr(d_pos), int(n_part), int(n_mesh), float(omega_m), int(nbins),
                                        k.ctypes.data_as(C.POINTER(C.c_double)),
                                        pk.ctypes.data_as(C.POINTER(C.c_double)),

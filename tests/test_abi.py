@@ -69,3 +69,28 @@ def test_null_arguments(pm):
     assert pm.lib.pm_init(None, None) == pm.PM_ERR_INVALID_ARG
     assert pm.lib.pm_step(None) == pm.PM_ERR_INVALID_ARG
     pm.lib.pm_destroy(None)
+
+
+def test_noalloc_wrapper_rejects_bad_position_arrays_before_any_call(pm, monkeypatch):
+    """The allocation-free P(k) reads 3 * n doubles at the pointer: a flat array, an FP32 array or a tensor
+    on the CPU must be refused by the binding with ValueError, before the library is reached."""
+    import numpy as np
+    import torch
+
+    calls = []
+
+    class NoLib:
+        def __getattr__(self, name):
+            calls.append(name)
+            raise AssertionError(f"library reached: {name}")
+
+    monkeypatch.setattr(pm, "lib", NoLib())
+    bad = [torch.zeros(300, dtype=torch.float64),            # flat (3N,)
+           torch.zeros((100, 3), dtype=torch.float32),       # FP32 read as FP64
+           torch.zeros((100, 4), dtype=torch.float64),       # wrong row width
+           torch.zeros((100, 3), dtype=torch.float64),       # host tensor, not on the current device
+           np.zeros(300), np.zeros((100, 3), dtype=np.float32)]
+    for arr in bad:
+        with pytest.raises(ValueError):
+            pm.pm_power_spectrum_noalloc(arr, 32, 0.31, 8)
+    assert calls == []

@@ -6,7 +6,9 @@ device memory handed entirely to the application's own sub-allocator).  It
 runs on a fixed scratch array inside the library, so after its first call on
 a device it must not change the device's free memory, and two calls in a row
 must both reproduce pm_power_spectrum of a context holding the same particles.
-This file is collected last on purpose.
+The mesh sizes cover the generic mixed-radix FFT path (8, 24, 48, whose
+twiddles the entry point computes on the device) and the compiled passes
+(32, 64).  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -16,15 +18,16 @@ pytestmark = pytest.mark.gpu
 OM, BOX = 0.31, 320.0
 
 
-def test_noalloc_power_spectrum_matches_context_version():
+@pytest.mark.parametrize("n,npart_side", [(8, 6), (24, 13), (32, 32), (48, 17), (64, 20)])
+def test_noalloc_power_spectrum_matches_context_version(n, npart_side):
     import torch
     from paper_2607_17929_gb300 import build
     build.build()
     from paper_2607_17929_gb300 import ics, pm
 
-    n, nbins = 32, 14
-    pos, mom = ics.zeldovich_ics(n, BOX, OM, 0.67, 1 / 101, 1 / 101, 11)
-    ctx = pm.PM(n, n ** 3, BOX, OM, 100.0, 0.0, 100, pm.PM_FP64)
+    nbins = n // 2 - 2
+    pos, mom = ics.zeldovich_ics(npart_side, BOX * npart_side / n, OM, 0.67, 1 / 101, 1 / 101, 11 + n)
+    ctx = pm.PM(n, npart_side ** 3, BOX, OM, 100.0, 0.0, 100, pm.PM_FP64)
     ctx.set_particles(pos, mom)
     k0, pk0, nm0 = ctx.power_spectrum(nbins)
     ctx.close()
@@ -57,6 +60,7 @@ def test_noalloc_rejects_sizes_above_its_scratch():
     with pytest.raises(pm.PMError) as e:
         pm.pm_power_spectrum_noalloc(d_pos, 32, OM, 4096)
     assert e.value.status == pm.PM_ERR_UNSUPPORTED_SIZE
+    # host memory of the right layout reaches the library, which rejects it
     with pytest.raises(pm.PMError) as e:
-        pm.pm_power_spectrum_noalloc(d_pos.cpu(), 32, OM, 8)
+        pm.pm_power_spectrum_noalloc(d_pos.cpu().numpy(), 32, OM, 8)
     assert e.value.status == pm.PM_ERR_INVALID_ARG

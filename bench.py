@@ -407,6 +407,100 @@ def schedule_phases(pm, torch, n, n_part, box, d_pos, d_mom, stream, block=10):
     return out
 
 
+def config2_bench(pm, torch, n=256, box=1000.0, seed=2, checkpoints=(10, 50, 100), nbins=None):
+    """FP64 against mixed precision over the whole 100-step schedule (z = 100 -> 0) at 256^3 mesh and
+    particles in a 1 Gpc/h box: per-stage ms and per-kernel GB/s of both forms, and the relative L2 of each
+    mixed field against the FP64 GPU path at steps 10, 50 and 100, and P(k) at z = 0.  Both contexts step in
+    lockstep from the same Zel'dovich/BBKS initial conditions; field differences are taken on the device."""
+    stream = torch.cuda.current_stream()
+    probe = pm.PM(8, 8, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED)
+    a_n, dtau, _ = probe.schedule()
+    probe.close()
+    pos, mom = make_ics(n, box, seed, a_n[0], half_step_back(a_n[0], dtau[0], box))
+    d_pos, d_mom = torch.from_numpy(pos).cuda(), torch.from_numpy(mom).cuda()
+    del pos, mom
+    sims = {name: pm.PM(n, n ** 3, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, prec, 0, stream)
+            for name, prec in (("fp64", pm.PM_FP64), ("mixed", pm.PM_MIXED))}
+    for g in sims.values():
+        g.set_particles(d_pos, d_mom)
+    nc = n ** 3
+    nh = n * n * (n // 2 + 1)
+    bufs = {k: torch.empty(nc, dtype=torch.float64, device="cuda") for k in ("fp64", "mixed")}
+    tbufs = {k: torch.empty(2 * nh, dtype=torch.float64, device="cuda") for k in ("fp64", "mixed")}
+    pbufs = {k: (torch.empty((n ** 3, 3), dtype=torch.float64, device="cuda"),
+                 torch.empty((n ** 3, 3), dtype=torch.float64, device="cuda")) for k in ("fp64", "mixed")}
+
+    def rel_field(get, names, bb):
+        num = den = 0.0
+        for nm in names:
+            for k in ("fp64", "mixed"):
+                get(sims[k].ctx, nm, bb[k])
+            num += float(torch.sum((bb["mixed"] - bb["fp64"]) ** 2))
+            den += float(torch.sum(bb["fp64"] ** 2))
+        return math.sqrt(num / den) if den > 0 else 0.0
+
+    errors = {}
+    ms = {k: [] for k in sims}
+    kern = {k: {} for k in sims}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in sims:
+        pm.pm_get_timings(sims[k].ctx)
+    done = 0
+    for cp in checkpoints:
+        for k, g in sims.items():
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(cp - done):
+                g.step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms[k].append((cp - done, ev0.elapsed_time(ev1)))
+            per, _ = pm.pm_get_timings(g.ctx)
+            for key, v in per.items():
+                kern[k][key] = kern[k].get(key, 0.0) + v * (cp - done)
+        done = cp
+        e = {"phi": rel_field(pm.pm_get_field, ["phi"], bufs), "chi": rel_field(pm.pm_get_field, ["chi"], bufs),
+             "B": rel_field(pm.pm_get_field, ["Bx", "By", "Bz"], bufs),
+             "h": rel_field(pm.pm_get_tensor, ["h+", "hx"], tbufs)}
+        for k in sims:
+            pm.pm_get_particles(sims[k].ctx, *pbufs[k])
+        torch.cuda.synchronize()
+        dx = torch.remainder(pbufs["mixed"][0] - pbufs["fp64"][0] + 0.5, 1.0) - 0.5
+        disp = torch.remainder(pbufs["fp64"][0] - d_pos + 0.5, 1.0) - 0.5
+        e["x_rms_cells"] = float(torch.sqrt(torch.mean(dx ** 2))) * n
+        e["x_rel_to_displacement"] = float(torch.linalg.norm(dx) / torch.linalg.norm(disp))
+        e["u"] = float(torch.linalg.norm(pbufs["mixed"][1] - pbufs["fp64"][1]) / torch.linalg.norm(pbufs["fp64"][1]))
+        errors[f"step_{cp}"] = {key: float(f"{v:.3e}") for key, v in e.items()}
+    nb = nbins or n // 2
+    pk = {k: pm.pm_power_spectrum(g.ctx, nb) for k, g in sims.items()}
+    kk, p64, nm = pk["fp64"]
+    _, pmx, _ = pk["mixed"]
+    half = [b for b in range(1, nb) if nm[b] > 0 and b <= n // 4]
+    dev = [abs(pmx[b] / p64[b] - 1.0) for b in half]
+    peak = load_peaks()[0]
+    out = {"workload": f"{n}^3 mesh, {n}^3 particles, box {box:.0f} Mpc/h, seed {seed}, LCDM Om={OM} h={H}, "
+                       f"z = 100 -> 0 in {N_STEPS_SCHEDULE} steps, FP64 and mixed in lockstep from the same ICs",
+           "errors_mixed_vs_fp64": errors,
+           "pk_z0_max_rel_dev_to_half_nyquist": float(f"{max(dev):.3e}"),
+           "pk_z0": {"k": [round(float(kk[b]), 4) for b in half], "fp64": [float(f"{p64[b]:.6e}") for b in half],
+                     "mixed_over_fp64_minus_1": [float(f"{pmx[b] / p64[b] - 1.0:.3e}") for b in half]}}
+    for k in sims:
+        steps = sum(c for c, _ in ms[k])
+        step_ms = sum(t for _, t in ms[k]) / steps
+        km = {key: v / steps for key, v in kern[k].items()}
+        mixed = k == "mixed"
+        gbs = {key: round(kernel_bytes(key, n, n ** 3, mixed) / (km[key] * 1e-3) / 1e9, 1)
+               for key in KERNELS if km.get(key, 0) > 0.01}
+        out[k] = {"ms_per_step": round(step_ms, 3), "particle_updates_per_s": n ** 3 / (step_ms * 1e-3),
+                  "kernels_ms": {key: round(v, 4) for key, v in km.items()},
+                  "kernels_gbs": gbs, "step_roofline_frac": round(
+                      method_bytes_per_update(mixed) * n ** 3 / (step_ms * 1e-3) / 1e9 / peak, 4)}
+    out["speedup_mixed_over_fp64"] = round(out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"], 2)
+    for g in sims.values():
+        g.close()
+    return out
+
+
 def _load_cufft():
     import ctypes
     import glob
@@ -478,9 +572,11 @@ def load_bf16_peak():
         return 1900.0
 
 
-def cpu_oracle_rate(n, steps, box):
-    """Particle updates per second of the FP64 C oracle (single thread) on an n^3 sample."""
+def cpu_oracle_rate(n, steps, box, threads=1):
+    """Particle updates per second of the FP64 C oracle on an n^3 sample; threads = 0 uses every core (the
+    oracle's independent loops carry OpenMP pragmas; results do not depend on the thread count)."""
     from oracle import oracle as O
+    O.set_threads(threads)
     s = O.OracleSim(n, n ** 3, OM, box, ZI, 0.0, N_STEPS_SCHEDULE)
     a_m = O.a_after(s.a_n[0], -0.5 * s.dtau[0], OM, s.h0)
     pos, mom = make_ics(n, box, SEED, s.a_n[0], a_m)
@@ -489,7 +585,7 @@ def cpu_oracle_rate(n, steps, box):
     for _ in range(steps):
         s.step()
     dt = time.perf_counter() - t0
-    return n ** 3 * steps / dt, dt
+    return n ** 3 * steps / dt, dt, O.set_threads(threads)
 
 
 METRIC = "particle-updates/s per full PM step at 512^3 (mixed precision)"
@@ -506,13 +602,15 @@ def workload_config(n, box, warmup, steps, world):
 
 
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    """The reference arm: the FP64 CPU oracle on all host cores, on a bounded sample of the workload (a 64^3
+    box with the benchmark's cell size, same recipe); config.workload names that sample."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     n = 64
     box = CELL_MPCH * n
     from oracle import oracle as O
+    cores = O.set_threads(0)
     s = O.OracleSim(n, n ** 3, OM, box, ZI, 0.0, N_STEPS_SCHEDULE)
     a_m = O.a_after(s.a_n[0], -0.5 * s.dtau[0], OM, s.h0)
     pos, mom = make_ics(n, box, SEED, s.a_n[0], a_m)
@@ -524,15 +622,17 @@ def run_reference(args):
         s.step()
     dt = time.perf_counter() - t0
     value = n ** 3 * args.steps / dt
-    sample = f"{args.steps} oracle steps of the same recipe at {n}^3 (box {box:.0f} Mpc/h, same cell size)"
+    sample = (f"{args.steps} oracle steps of the same recipe at {n}^3 (box {box:.0f} Mpc/h, the cell size of the "
+              f"{args.n}^3 benchmark box), steps {args.warmup}..{args.warmup + args.steps - 1}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value,
         "unit": "particle-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.n, CELL_MPCH * args.n, args.warmup, args.steps, args.gpus),
-        "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": sample + "; the FP64 CPU oracle, single thread", "host": host_cpu()},
+        "config": dict(workload_config(n, box, args.warmup, args.steps, args.gpus),
+                       sampled_from=f"the {args.n}^3 mesh / {args.n}^3 particle benchmark workload"),
+        "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample + f"; the FP64 CPU oracle on {cores} threads", "host": host_cpu()},
         "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -554,6 +654,7 @@ def main():
     ap.add_argument("--no-correction", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
+    ap.add_argument("--no-config2", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=10)
     args = ap.parse_args()
@@ -650,6 +751,12 @@ def main():
         phases = schedule_phases(pm, torch, n, n_part, box, d_pos, d_mom, stream)
         torch.cuda.empty_cache()
 
+    # FP64 vs mixed over the whole schedule at 256^3 / 1 Gpc/h
+    config2 = None
+    if not args.no_config2:
+        config2 = config2_bench(pm, torch)
+        torch.cuda.empty_cache()
+
     # FP64 path on the same workload
     fp64 = None
     if not args.no_fp64:
@@ -713,10 +820,13 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         nc_ = 96
-        rate, dt = cpu_oracle_rate(nc_, 2, CELL_MPCH * nc_)
-        cpu = {"value": rate, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+        rate, dt, cores = cpu_oracle_rate(nc_, 2, CELL_MPCH * nc_, threads=0)
+        rate1, dt1, _ = cpu_oracle_rate(nc_, 1, CELL_MPCH * nc_, threads=1)
+        cpu = {"value": rate, "unit": "particle-updates/s", "cores": cores, "kind": "oracle",
                "sample": f"2 steps of the same recipe at {nc_}^3 (box {CELL_MPCH * nc_:.0f} Mpc/h, same cell "
-                         f"size) after its bootstrap, single thread, {dt:.1f} s", "host": host_cpu()}
+                         f"size) after its bootstrap, all {cores} host threads, {dt:.1f} s", "host": host_cpu(),
+               "single_thread": {"value": rate1, "cores": 1, "seconds": round(dt1, 1),
+                                 "sample": f"1 step at {nc_}^3 after its bootstrap"}}
 
     if rank == 0:
         h2d = 2 * 3 * 8 * n_part
@@ -738,6 +848,7 @@ def main():
             "correction": correction,
             "cufft_comparison": cufft,
             "schedule_phases": phases,
+            "config2_fp64_vs_mixed": config2,
             "e2e": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                     "how": "pm_put_particles(pinned host f64 pos, mom) + pm_step + pm_get_particles(pinned host)"},

@@ -19,12 +19,20 @@ _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
 def build_oracle(force: bool = False) -> str:
-    """Compile pm_oracle.c with gcc into liboracle.so next to it."""
+    """Compile pm_oracle.c with gcc into liboracle.so next to it (with OpenMP where gcc has it)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.call(base + ["-fopenmp"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _SO)
     return _SO
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's OpenMP loops (0: all cores); returns the count in use (1 without OpenMP).
+    Results do not depend on it: the parallel loops have independent iterations and no reductions."""
+    return int(lib().or_set_threads(int(n)))
 
 
 _lib = None
@@ -34,6 +42,8 @@ def lib():
     global _lib
     if _lib is None:
         L = C.CDLL(build_oracle())
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         L.or_conformal_hubble.restype = C.c_double
         L.or_conformal_hubble.argtypes = [C.c_double, C.c_double, C.c_double]
         L.or_tau_between.restype = C.c_double

@@ -8,6 +8,10 @@
  *
  * Everything is written the obvious way: full complex 3D DFTs (own
  * recursive mixed-radix FFT), sequential sums, one loop per equation.
+ * Loops whose iterations are independent (the lines of an FFT pass, mesh
+ * cells, particles of the kick and drift) carry OpenMP pragmas: there are no
+ * parallel reductions, so every result is bit-identical for any thread
+ * count (or_set_threads; built without OpenMP the pragmas are ignored).
  * Mesh arrays are [z][y][x] with x fastest; positions are absolute box
  * coordinates in [0,1) (box length L = 1, c = 1).
  *
@@ -34,6 +38,9 @@
  */
 #include <complex.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -176,12 +183,28 @@ void or_fft1d(cplx *data, long n, long stride, int sign)
 void or_fft3d(cplx *data, int n, int sign)
 {
     long N = n;
+#pragma omp parallel for schedule(static) if (N >= 32)
     for (long z = 0; z < N; z++)
         for (long y = 0; y < N; y++) or_fft1d(data + (z * N + y) * N, N, 1, sign);
+#pragma omp parallel for schedule(static) if (N >= 32)
     for (long z = 0; z < N; z++)
         for (long x = 0; x < N; x++) or_fft1d(data + z * N * N + x, N, N, sign);
+#pragma omp parallel for schedule(static) if (N >= 32)
     for (long y = 0; y < N; y++)
         for (long x = 0; x < N; x++) or_fft1d(data + y * N + x, N, N * N, sign);
+}
+
+/* Threads of the OpenMP loops (n <= 0: all cores); returns the count in use, 1 without OpenMP. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    else omp_set_num_threads(omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Python-friendly wrapper: interleaved (re, im) doubles. */
@@ -264,6 +287,7 @@ void or_deposit_mass(int n, const double *pos, long np, double mass, double *rho
 void or_gradient(const double *f, int n, int d, double *g)
 {
     long N = n;
+#pragma omp parallel for schedule(static) if (N >= 32)
     for (long z = 0; z < N; z++)
         for (long y = 0; y < N; y++)
             for (long x = 0; x < N; x++) {
@@ -368,6 +392,7 @@ typedef struct {
 void or_laplacian7(const double *f, int n, double *out)
 {
     long N = n;
+#pragma omp parallel for schedule(static) if (N >= 32)
     for (long z = 0; z < N; z++)
         for (long y = 0; y < N; y++)
             for (long x = 0; x < N; x++) {
@@ -495,6 +520,7 @@ void or_sources(int n, const or_solve_params *sp, const double *s00, const doubl
         or_gradient(psi, n, d, gpsi + d * nc);
     }
     const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma omp parallel for schedule(static) if (n >= 32)
     for (size_t c = 0; c < nc; c++) {
         double dphi_dtau = (phi_prev[c] - phi_prev2[c]) / sp->dtau_prev2;
         for (int i = 0; i < 3; i++) F[i * nc + c] = g4 / (a * a) * s0i[i * nc + c] - dphi_dtau * gpsi[i * nc + c];
@@ -548,6 +574,7 @@ void or_fourier_solve(int n, const or_solve_params *sp, cplx *Rk /* in: R, out: 
     else
         cphi = 3.0 * sp->hc / sp->dtau_prev + 3.0 * sp->hc * sp->hc;
     const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma omp parallel for schedule(static) if (N >= 32)
     for (long z = 0; z < N; z++)
         for (long y = 0; y < N; y++)
             for (long x = 0; x < N; x++) {
@@ -653,6 +680,7 @@ void or_kick_drift(int n, double *pos, double *mom, long np, double a_kick, doub
         if (!newtonian)
             for (int j = 0; j < 3; j++) or_gradient(B + j * nc, n, d, gB + (d * 3 + j) * nc); /* d_d B_j */
     }
+#pragma omp parallel for schedule(static) if (np >= 4096)
     for (long p = 0; p < np; p++) {
         double *x = pos + 3 * p, *u = mom + 3 * p;
         double K[3];

@@ -13,6 +13,8 @@ import pytest
 from oracle import oracle as O
 from paper_2607_17929_gb300 import ics
 
+from mixed_bounds import mixed_violations
+
 pytestmark = pytest.mark.gpu
 
 OM, H = 0.31, 0.67
@@ -136,9 +138,8 @@ def test_mixed_clustered_tile_needs_several_chunks(pm):
         for k, v in compare(orc, g, n).items():
             worst[k] = max(worst.get(k, 0.0), v)
     g.close()
-    assert worst["phi"] < 1e-5 and worst["R"] < 1e-5 and worst["u"] < 1e-5, worst
-    for k in ("chi", "B", "Fx", "Sxx", "h+", "hx"):
-        assert worst[k] < 1e-3, (k, worst[k])
+    print("mixed clustered vs oracle worst rel L2:", {k: f"{v:.2e}" for k, v in worst.items()})
+    assert not mixed_violations(worst), mixed_violations(worst)
 
 
 def test_fp64_newtonian_zero_net_momentum(pm):
@@ -239,9 +240,8 @@ def test_power_spectrum_matches_oracle(pm):
 
 
 def test_mixed_precision_ten_steps_32cubed(pm):
-    """Mixed form against the FP64 oracle.  FP32 fields and FFT carry ~1e-7 relative rounding per
-    operation; over the few hundred operations of a step and 10 steps the potentials stay within 1e-5,
-    the second-order quantities (chi, B, h built from gradients and momenta) within 1e-3.  Positions are
+    """Mixed form against the FP64 oracle, every field within its bound in mixed_bounds.py (about five
+    times the worst measured value; each bound is derived there from the FP32 arithmetic).  Positions are
     cell + f32 offset: each drift rounds the offset to 2^-24 of a cell, so after 10 steps the rms
     position error stays below 10 * 2^-24 ~ 6e-7 cell plus the f32 velocity error times the displacement."""
     orc, g, pos, mom = make_pair(pm, 32, 32, 320.0, 1, pm.PM_MIXED)
@@ -260,10 +260,8 @@ def test_mixed_precision_ten_steps_32cubed(pm):
     g.close()
     print("mixed vs oracle worst rel L2:", {k: f"{v:.2e}" for k, v in worst.items()},
           f"dx/disp {dx:.2e} rms dx {rms_cells:.2e} cell")
-    assert worst["phi"] < 1e-5 and worst["R"] < 1e-5
-    assert worst["u"] < 1e-5 and rms_cells < 1e-6 and dx < 1e-4
-    for k in ("chi", "B", "Fx", "Sxx", "h+", "hx"):
-        assert worst[k] < 1e-3, (k, worst[k])
+    assert not mixed_violations(worst), mixed_violations(worst)
+    assert rms_cells < 1e-6 and dx < 1e-4
 
 
 @pytest.mark.parametrize("n,n_side,box,newtonian", [(64, 64, 640.0, False), (128, 48, 1280.0, True)])
@@ -279,8 +277,6 @@ def test_mixed_precision_tuned_fft_sizes(pm, n, n_side, box, newtonian):
     p_o, _ = orc.particles()
     rms_cells = float(np.sqrt(np.mean(wrapdiff(p_g, p_o) ** 2)) * n)
     g.close()
-    assert e["phi"] < 1e-5 and e["u"] < 1e-5 and rms_cells < 1e-6, (e, rms_cells)
-    if not newtonian:
-        assert e["R"] < 1e-5
-        for k in ("chi", "B", "Fx", "Sxx", "h+", "hx"):
-            assert e[k] < 1e-3, (k, e[k])
+    print(f"mixed {n}^3 vs oracle:", {k: f"{v:.2e}" for k, v in e.items()}, f"rms dx {rms_cells:.2e} cell")
+    assert not mixed_violations(e), mixed_violations(e)
+    assert rms_cells < 1e-6, rms_cells

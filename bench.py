@@ -197,8 +197,10 @@ def ensemble_specs():
 
 
 def ensemble_bench(pm, torch, steps, warmup):
-    """boxes*steps/s of the batched ensemble (one captured graph per step, autotuned stream count) against
-    looping the single-box pm_step over the same boxes on one stream.  Inputs resident in HBM."""
+    """boxes*steps/s of the batched ensemble (one captured graph per step; the autotuner picks the FFT and
+    deposit shapes per mesh size, the stream count and per-box or batched particle kernels) against looping
+    the single-box pm_step over the same boxes on one stream, and the mode the tuner did not pick.  Inputs
+    resident in HBM."""
     specs = ensemble_specs()
     inputs = []
     t_ic = time.perf_counter()
@@ -243,31 +245,32 @@ def ensemble_bench(pm, torch, steps, warmup):
         pm.pm_ensemble_set_particles(e, b, p, u)
     pm.pm_ensemble_step(e, use_graph=False)
     k = pm.pm_ensemble_tune(e)
-    shapes = {}
+    _, tuned_batched = pm.pm_ensemble_get_mode(e)
+    shapes, dep_shapes = {}, {}
     for b, (n, _, _) in enumerate(specs):
         if n not in shapes:
             shapes[n] = pm.pm_fft_shapes(pm.pm_ensemble_box(e, b), -2, -2)
+            dep_shapes[n] = pm.pm_deposit_shape(pm.pm_ensemble_box(e, b), -2)
     es = torch.cuda.ExternalStream(pm.pm_ensemble_stream(e))
-    for _ in range(warmup):
-        pm.pm_ensemble_step(e, use_graph=True)
-    pm.pm_ensemble_sync(e)
-    ev0.record(es)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        pm.pm_ensemble_step(e, use_graph=True)
-    ev1.record(es)
-    pm.pm_ensemble_sync(e)
-    wall_ms = 1e3 * (time.perf_counter() - t0) / steps
-    ev1.synchronize()
-    ens_ms = ev0.elapsed_time(ev1) / steps
-    # the same streams without graphs, for reference
-    ev0.record(es)
-    for _ in range(steps):
-        pm.pm_ensemble_step(e, use_graph=False)
-    ev1.record(es)
-    pm.pm_ensemble_sync(e)
-    ev1.synchronize()
-    nog_ms = ev0.elapsed_time(ev1) / steps
+
+    def run(batched, use_graph):
+        pm.pm_ensemble_set_batched(e, batched)
+        for _ in range(warmup):
+            pm.pm_ensemble_step(e, use_graph=use_graph)
+        pm.pm_ensemble_sync(e)
+        ev0.record(es)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            pm.pm_ensemble_step(e, use_graph=use_graph)
+        ev1.record(es)
+        pm.pm_ensemble_sync(e)
+        wall = 1e3 * (time.perf_counter() - t0) / steps
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / steps, wall
+
+    ens_ms, wall_ms = run(tuned_batched, True)            # the tuner's choice
+    other_ms, _ = run(not tuned_batched, True)            # the other particle-kernel mode, same streams
+    nog_ms, _ = run(tuned_batched, False)                 # the tuner's choice without graphs
     pm.pm_ensemble_destroy(e)
     del inputs
     torch.cuda.empty_cache()
@@ -275,16 +278,21 @@ def ensemble_bench(pm, torch, steps, warmup):
     return {"metric": "boxes*steps/s", "value": nb / (ens_ms * 1e-3), "ms_per_step": ens_ms,
             "host_wall_ms_per_step": wall_ms, "loop_value": nb / (loop_ms * 1e-3), "loop_ms_per_step": loop_ms,
             "speedup_over_loop": loop_ms / ens_ms, "streams": k, "no_graph_ms_per_step": nog_ms,
+            "batched_particle_kernels": tuned_batched,
+            ("per_box_ms_per_step" if tuned_batched else "batched_ms_per_step"): other_ms,
             "fft_shapes": {str(n): list(v) for n, v in shapes.items()},
+            "deposit_shapes": {str(n): v for n, v in dep_shapes.items()},
             "particle_updates_per_s": part / (ens_ms * 1e-3), "steps": steps, "warmup": warmup,
             "config": "48 boxes: 16 x 64^3, 16 x 128^3, 16 x 192^3 mesh, one particle per cell, box U(200,1000) "
                       "Mpc/h, seeds 1000+b, mixed precision, same Zel'dovich/BBKS recipe at z=100",
             "ic_seconds": round(t_ic, 1)}
 
 
-def correction_bench(pm, torch, reps=20):
+def correction_bench(pm, torch, reps=20, train=True):
     """Learned force correction at its 256^3 workload (500 Mpc/h, Newtonian): network forward (4 conv layers on
-    the tensor cores), one training step, and the plain vs corrected step, all timed with CUDA events."""
+    the tensor cores), one training step, and the plain vs corrected step, all timed with CUDA events; then a
+    short training run and its gain on two held-out seeds (rms displacement and P(k) against the 512^3-mesh run
+    of the same particles)."""
     n, box = 256, 500.0
     probe = pm.PM(8, 8, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED, pm.PM_NEWTONIAN)
     a_n, dtau, _ = probe.schedule()
@@ -320,6 +328,31 @@ def correction_bench(pm, torch, reps=20):
     train_ms = timed(lambda: pm.pm_net_backward(net, tgt, want_loss=False), 5)
     sim.close()
     pm.pm_net_destroy(net)
+    gain = None
+    if train:
+        # what the trained network gains: trained on 8 seeds (snapshots at steps 90 and 99), evaluated on two
+        # held-out seeds against the plain 256^3 run, both compared with the 512^3-mesh run of the same particles
+        from paper_2607_17929_gb300 import correction as CR
+        t0 = time.perf_counter()
+        tnet = pm.pm_net_create(n, 1)
+        snaps = {90, 99}
+        CR.calibrate(pm, torch, tnet, 999, snaps, n, box)
+        pairs = CR.make_pairs(pm, torch, tnet, list(range(1000, 1008)), snaps, n, box, log=lambda *_: None)
+        losses = CR.train(pm, torch, tnet, pairs, 600, log=lambda *_: None)
+        ev_val = CR.explained_variance(pm, torch, tnet, CR.make_pairs(pm, torch, tnet, [3000], snaps, n, box,
+                                                                       log=lambda *_: None))
+        del pairs
+        torch.cuda.empty_cache()
+        evals = [CR.evaluate(pm, torch, tnet, s, n, box, log=lambda *_: None) for s in (5000, 5001)]
+        pm.pm_net_destroy(tnet)
+        gain = {"training": "8 seeds (1000-1007), snapshots at steps 90 and 99, 600 Adam steps; validation seed 3000",
+                "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)],
+                "explained_variance_validation": [round(e["explained"], 3) for e in ev_val],
+                "held_out": [{"seed": e["seed"],
+                              **{k: {kk: round(vv, 4) for kk, vv in e[k].items()} for k in ("plain", "corrected")},
+                              "ms_per_step": {k: round(v, 3) for k, v in e["ms_per_step"].items()}} for e in evals],
+                "seconds": round(time.perf_counter() - t0, 1)}
+        torch.cuda.empty_cache()
     cells = n ** 3
     # algorithmic work of the network, and the MMA work the kernels issue: layer 1 packs 8 offsets x 2
     # channels per k16 step (4 steps), layers 2-3 16 x 16 per offset, layer 4 16 x 8 per offset
@@ -328,7 +361,7 @@ def correction_bench(pm, torch, reps=20):
     peak = load_bf16_peak()
     return {"workload": "256^3 mesh and particles, 500 Mpc/h, Newtonian, mixed; network 2-16-16-16-3, 3^3 conv, "
                         "BF16/FP32, He-initialised weights (timing does not depend on them)",
-            "plain_step_ms": round(plain_ms, 3), "corrected_step_ms": round(corr_ms, 3),
+            "plain_step_ms": round(plain_ms, 3), "corrected_step_ms": round(corr_ms, 3), "trained_gain": gain,
             "forward_ms": round(fwd_ms, 3), "forward_backward_ms": round(train_ms, 3),
             "roofline": {"bound": "tensor", "kernel": "k_conv_in2 + k_conv_tc (4 layers)",
                          "achieved": round(useful / (fwd_ms * 1e-3) / 1e12, 1), "peak": peak, "unit": "TFLOP/s",

@@ -245,6 +245,20 @@ pm_status pm_get_timings(pm_ctx *ctx, double *ms, int n, int64_t *launches);
  * Errors: INVALID_ARG (force_* outside -2..2), STATE, CUDA. */
 pm_status pm_fft_shapes(pm_ctx *ctx, int32_t force_y, int32_t force_z, int32_t *y_shape, int32_t *z_shape);
 
+/* Shape of the projection's shared-memory bins (Sec. 2.1, the particle-mesh
+ * projection): the number of particle records one 8^3 vertex tile stages at
+ * a time.  Shape 0: 960 records (FP32) / 640 (FP64), the default; shape 1:
+ * 768 / 512.  Fewer records per chunk suit early, nearly uniform loads, more
+ * suit clustered late loads (more tiles then fit in one chunk).  Both shapes
+ * compute the same sums (only the order of additions inside a cell may
+ * differ).  force 0 or 1 selects a shape; -2 keeps the current one; -1 times
+ * the deposit of the context's current state with both shapes and keeps the
+ * faster one (the context must hold particles and be between steps; the
+ * trial deposits write into internal scratch, so the fields pm_get_field
+ * returns do not change).  *shape (may be NULL) receives the shape in use.
+ * Errors: INVALID_ARG (force outside -2..1), STATE, CUDA. */
+pm_status pm_deposit_shape(pm_ctx *ctx, int32_t force, int32_t *shape);
+
 /* Checkpoint: write / read the full state (config, step, particles,
  * phi_{n-1}, chi_{n-1}, phi_{n-2}, tensor state) to / from a host file.
  * pm_load requires a context created with the same config.
@@ -293,12 +307,26 @@ pm_status pm_ensemble_stream(pm_ensemble *e, void **stream);
  * smaller boxes round-robin on the others. */
 pm_status pm_ensemble_set_streams(pm_ensemble *e, int32_t n_streams);
 
-/* Autotuner: first the FFT column-pass shapes of every distinct mesh size
- * (pm_fft_shapes with -1 on the first box of that size, the choice copied to
- * the others; no box advances), then for each candidate number of streams
- * (1, 2, 4, 8, at most nbox) one untimed and two timed graph-captured
- * ensemble steps, keeping the fastest; *n_streams receives it.  Each stream
- * trial advances every box by three steps. */
+/* Batched particle kernels (1) or per-box steps (0, the default).  Batched:
+ * one projection launch and one gather + kick + drift launch each cover every
+ * box of a precision, as a work list of (box, tile) items (a CTA finds its box
+ * in a prefix table of the boxes' tile counts and reads that box's parameters
+ * from the launch's parameter block); the transforms, Fourier solves and
+ * sorts of the boxes run on the ensemble's streams in between.  Errors:
+ * INVALID_ARG. */
+pm_status pm_ensemble_set_batched(pm_ensemble *e, int32_t batched);
+
+/* Current stream count and batched flag (either pointer may be NULL). */
+pm_status pm_ensemble_get_mode(pm_ensemble *e, int32_t *n_streams, int32_t *batched);
+
+/* Autotuner: first the FFT column-pass shapes and the projection's bin shape
+ * of every distinct mesh size and precision (pm_fft_shapes and
+ * pm_deposit_shape with -1 on the first box of that size, the choice copied
+ * to the others; no box advances), then for each candidate number of streams
+ * (1, 2, 4, 8, at most nbox), per-box and batched, one untimed and two timed
+ * graph-captured ensemble steps, keeping the fastest; *n_streams receives the
+ * stream count (pm_ensemble_get_mode reports the batched flag).  Each trial
+ * advances every box by three steps. */
 pm_status pm_ensemble_tune(pm_ensemble *e, int32_t *n_streams);
 
 /* ------------------------------------------------------------------------

@@ -131,6 +131,8 @@ template <class P> P *kernel_ptr(P *p)
     return nullptr;
 }
 
+}  // namespace
+
 StepScalars scalars(const Ctx &c, int k, bool bootstrap)
 {
     const Background bg(c.cfg.omega_m, c.h0);
@@ -173,6 +175,8 @@ template <class T> void **spec_ptrs(Ctx &c, void **p)
     return p;
 }
 
+namespace {
+
 template <class T> pm_status do_project(Ctx &c, bool bootstrap)
 {
     StepScalars s = scalars(c, c.step, bootstrap);
@@ -180,6 +184,8 @@ template <class T> pm_status do_project(Ctx &c, bool bootstrap)
     CKL("project");
     return PM_OK;
 }
+
+}  // namespace
 
 template <class T> pm_status do_solve(Ctx &c, bool bootstrap)
 {
@@ -219,6 +225,11 @@ template <class T> pm_status do_solve(Ctx &c, bool bootstrap)
     return PM_OK;
 }
 
+template pm_status do_solve<float>(Ctx &, bool);
+template pm_status do_solve<double>(Ctx &, bool);
+
+namespace {
+
 template <class T> pm_status do_update(Ctx &c)
 {
     StepScalars s = scalars(c, c.step, false);
@@ -232,6 +243,8 @@ template <class T> pm_status do_update(Ctx &c)
     return PM_OK;
 }
 
+}  // namespace
+
 // rotate the phi ring after step n: phi_{n-1} -> phi_{n-2}, phi_n -> phi_{n-1}
 void rotate(Ctx &c)
 {
@@ -240,6 +253,8 @@ void rotate(Ctx &c)
     c.iphi_prev = c.iphi_new;
     c.iphi_new = old2;
 }
+
+namespace {
 
 template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const double *mom, bool bootstrap)
 {
@@ -881,6 +896,27 @@ pm_status pm_fft_shapes(pm_ctx *ctx, int32_t force_y, int32_t force_z, int32_t *
     if (e != cudaSuccess) return cuda_fail(c, e, "pm_fft_shapes");
     if (y_shape) *y_shape = c.col_shape[0];
     if (z_shape) *z_shape = c.col_shape[1];
+    return PM_OK;
+}
+
+pm_status pm_deposit_shape(pm_ctx *ctx, int32_t force, int32_t *shape)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (force < -2 || force > 1) return fail(c, PM_ERR_INVALID_ARG, "pm_deposit_shape: shape outside -2..1");
+    if (force >= 0) c.dep_shape = force;
+    else if (force == -1) {
+        if (!c.have_particles || c.stage != 0 || c.step >= c.cfg.n_steps)
+            return fail(c, PM_ERR_STATE, "pm_deposit_shape: timing needs particles between steps");
+        const StepScalars s = scalars(c, c.step, false);
+        if (c.mixed) tune_deposit_shape<float>(c, s);
+        else tune_deposit_shape<double>(c, s);
+        cudaError_t e = c.stream ? cudaStreamSynchronize(c.stream) : cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "pm_deposit_shape");
+    }
+    if (shape) *shape = c.dep_shape;
     return PM_OK;
 }
 

@@ -94,6 +94,7 @@ struct Ctx {
     bool full_hc = false;       // PM_FULL_HC
     bool b_space = false;       // PM_B_SPACESPACE
     int col_shape[2] = {0, 0};  // shapes of the y and z column FFT passes (pm_fft_shapes)
+    int dep_shape = 0;          // record capacity of the deposit's shared-memory chunks (pm_deposit_shape)
 
     // schedule (host, FP64)
     std::vector<double> a_n, dtau, a_half;
@@ -172,6 +173,14 @@ template <class T>
 void launch_solve(Ctx &c, const StepScalars &s);
 template <class T>
 void launch_kick_drift(Ctx &c, const StepScalars &s);
+// batched forms for the ensemble: one launch over n boxes of one precision (and one deposit shape)
+template <class T>
+void launch_project_batch(Ctx *const *cs, const StepScalars *ss, int n, int shape, cudaStream_t st);
+template <class T>
+void launch_kick_batch(Ctx *const *cs, const StepScalars *ss, int n, cudaStream_t st);
+// times the deposit shapes on the context's current state and keeps the fastest (returns it)
+template <class T>
+int tune_deposit_shape(Ctx &c, const StepScalars &s);
 template <class T>
 void launch_sort(Ctx &c);
 template <class T>
@@ -195,6 +204,12 @@ template <class T>
 void launch_check_finite(Ctx &c, const double *d, int64_t n, int *d_flag);
 
 void launch_scan(Ctx &c);
+
+// step pieces shared by the single-box calls and the batched ensemble (pm_api.cu)
+StepScalars scalars(const Ctx &c, int k, bool bootstrap);
+template <class T>
+pm_status do_solve(Ctx &c, bool bootstrap);   // forward FFTs, Fourier solve, inverse FFTs
+void rotate(Ctx &c);                          // the phi ring after a completed step
 
 // compile-time-N FFT passes (pm_fft.cu)
 bool fast_fft_supported(int n);

@@ -9,6 +9,8 @@
 // registers.  No global atomics, and every mesh value is written once with
 // coalesced stores.  The same kernel assembles the configuration-space
 // sources of the field equations from phi_{n-1}, chi_{n-1}, phi_{n-2}.
+#include <algorithm>
+
 #include "pm_internal.cuh"
 
 namespace pm {
@@ -133,12 +135,15 @@ __device__ __forceinline__ T hc_remainder(const T *sphi, const T *schi, int vo, 
            T(1.5) * (p.hc * p.hc * expm1_minus_x(x) - T(2) * p.hc * dphi * em + dphi * dphi * (em + T(1)));
 }
 
-// particle records per shared-memory chunk: 960 (FP32) was the fastest of 640-1024 at 512^3, early and late
-template <class T> constexpr int dep_cap() { return sizeof(T) == 8 ? 640 : 960; }
+// Particle records per shared-memory chunk, the deposit's tunable "bin shape" (pm_deposit_shape): shape 0
+// (960 FP32) was the fastest of 640-1024 at 512^3 in early steps, shape 1 (768) is a little faster in the
+// first, unclustered steps and slower late.  Both keep three CTAs per SM in FP32.
+constexpr int NDEPSHAPES = 2;
+template <class T, int V> constexpr int dep_cap() { return sizeof(T) == 8 ? (V ? 512 : 640) : (V ? 768 : 960); }
 
-template <class T> size_t dep_smem()
+template <class T, int V> size_t dep_smem()
 {
-    return sizeof(T) * (12 * dep_cap<T>() + 2 * NFLD) +
+    return sizeof(T) * (12 * dep_cap<T, V>() + 2 * NFLD) +
            sizeof(int) * (3 * NREG + 64 + FLD * FLD + FLD);
 }
 
@@ -183,11 +188,11 @@ __device__ int block_exclusive_scan(int *v, int n, int *warp_tmp)
     return total;
 }
 
-template <class T>
-__global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project(const __grid_constant__ DepParams<T> p)
+// The deposit of one 8^3 vertex tile b of the box described by p (smem: dep_smem of this CAP).
+template <class T, int CAP>
+__device__ __forceinline__ void deposit_tile(const DepParams<T> &p, const int b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int CAP = dep_cap<T>();
     DepRec<T> *rec = reinterpret_cast<DepRec<T> *>(smem);            // [CAP]
     T *sphi = reinterpret_cast<T *>(rec + CAP);
     T *schi = sphi + NFLD;
@@ -199,7 +204,6 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
     int *xw = rowb + FLD * FLD;                                      // [FLD] wrapped x
 
     const int N = p.N, nt = p.nt, tid = threadIdx.x;
-    const int b = blockIdx.x;
     const int x0 = (b % nt) * TILE, y0 = ((b / nt) % nt) * TILE, z0 = (b / (nt * nt)) * TILE;
     if (tid < FLD * FLD) {
         const int ry = tid % FLD, rz = tid / FLD;
@@ -359,7 +363,8 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
             hi = t;
         }
         if ((tid & 31) == 0 && !p.newtonian)
-            atomicAdd(&p.k0slots[(b * (DEP_THREADS >> 5) + (tid >> 5)) & (NK0SLOTS - 1)], (double)hi + (double)lo);
+            atomicAdd(&p.k0slots[(blockIdx.x * (DEP_THREADS >> 5) + (tid >> 5)) & (NK0SLOTS - 1)],
+                      (double)hi + (double)lo);
     }
 
     // epilogue: assemble the field-equation sources at vertex o
@@ -395,8 +400,38 @@ __global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project
     reinterpret_cast<T *>(p.out.p[8])[go] = G4 * acc[7] - T(2) * Q[1][2];
 }
 
-// Sum the k = 0 slots: dscal[0] = sum over particles of the T^00 excess.
-__global__ void k_k0_reduce(double *dscal)
+template <class T, int V>
+__global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project(const __grid_constant__ DepParams<T> p)
+{
+    deposit_tile<T, dep_cap<T, V>()>(p, blockIdx.x);
+}
+
+// Several boxes in one launch (the batched ensemble): CTA j deposits tile j - first[i] of box i, the box whose
+// range [first[i], first[i+1]) holds j.  The boxes' parameters travel by value in the kernel's parameter space.
+constexpr int MAXBATCH = 48;
+template <class T> struct DepBatch {
+    int nbox;
+    int first[MAXBATCH + 1];
+    DepParams<T> box[MAXBATCH];
+};
+static_assert(sizeof(DepBatch<double>) < 32000, "kernel parameter space");
+
+template <class T, int V>
+__global__ void __launch_bounds__(DEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_project_batch(const __grid_constant__ DepBatch<T> q)
+{
+    int i = 0;
+    while (i + 1 < q.nbox && (int)blockIdx.x >= q.first[i + 1]) i++;
+    deposit_tile<T, dep_cap<T, V>()>(q.box[i], (int)blockIdx.x - q.first[i]);
+}
+
+// Sum the k = 0 slots: dscal[0] = sum over particles of the T^00 excess (block b: box b of a batch).
+struct K0Batch {
+    double *dscal[MAXBATCH];
+};
+__device__ void k0_reduce_one(double *dscal);
+__global__ void k_k0_reduce(double *dscal) { k0_reduce_one(dscal); }
+__global__ void k_k0_reduce_batch(const __grid_constant__ K0Batch q) { k0_reduce_one(q.dscal[blockIdx.x]); }
+__device__ void k0_reduce_one(double *dscal)
 {
     __shared__ double s[32];
     double v = 0.0;
@@ -491,7 +526,7 @@ __device__ __forceinline__ void gather_all(const Vtx4<T> *sv, const T *sbz, int 
 // the tile go to shared memory once; each thread then gathers the CIC value
 // and centred-difference gradients for one particle from there.
 template <class T>
-__global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_drift(const __grid_constant__ KdParams<T> p)
+__device__ __forceinline__ void kick_tile(const KdParams<T> &p, const int b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Vtx4<T> *sv = reinterpret_cast<Vtx4<T> *>(smem);              // [KNV]
@@ -502,7 +537,6 @@ __global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_dri
     int *rgs = roff + KT * KT + 2;                                 // 64 global row starts
     int *wtmp = rgs + KT * KT;                                     // 33
     const int N = p.N, nt = p.nt, tid = threadIdx.x;
-    const int b = blockIdx.x;
     const int x0 = (b % nt) * KT, y0 = ((b / nt) % nt) * KT, z0 = (b / (nt * nt)) * KT;
 
     if (tid < KV * KV) {
@@ -619,6 +653,27 @@ __global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_dri
         p.part[gi] = P;
         atomicAdd(&p.count[P.cell], 1);
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_drift(const __grid_constant__ KdParams<T> p)
+{
+    kick_tile<T>(p, blockIdx.x);
+}
+
+template <class T> struct KdBatch {
+    int nbox;
+    int first[MAXBATCH + 1];
+    KdParams<T> box[MAXBATCH];
+};
+static_assert(sizeof(KdBatch<double>) < 32000, "kernel parameter space");
+
+template <class T>
+__global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_batch(const __grid_constant__ KdBatch<T> q)
+{
+    int i = 0;
+    while (i + 1 < q.nbox && (int)blockIdx.x >= q.first[i + 1]) i++;
+    kick_tile<T>(q.box[i], (int)blockIdx.x - q.first[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -864,13 +919,8 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-template <class T>
-void launch_project(Ctx &c, const StepScalars &s)
+template <class T> DepParams<T> dep_params(const Ctx &c, const StepScalars &s)
 {
-    static std::atomic<uint64_t> attr{0};
-    if (first_on_device(attr)) {
-        cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dep_smem<T>());
-    }
     DepParams<T> p{};
     p.part = reinterpret_cast<const Particle<T> *>(c.part[c.cur]);
     p.start = c.start;
@@ -907,20 +957,67 @@ void launch_project(Ctx &c, const StepScalars &s)
     p.hc = (T)s.hc;
     p.n2 = (T)((double)c.N * (double)c.N);
     p.inv_g = 1.0 / (s.four_pi_g / (s.a * s.a) * n3);
+    return p;
+}
+
+template <class T, int V> void dep_attrs()
+{
+    static std::atomic<uint64_t> attr{0};
+    if (first_on_device(attr)) {
+        cudaFuncSetAttribute(k_project<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dep_smem<T, V>());
+        cudaFuncSetAttribute(k_project_batch<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dep_smem<T, V>());
+    }
+}
+
+template <class T>
+void launch_project(Ctx &c, const StepScalars &s)
+{
+    const DepParams<T> p = dep_params<T>(c, s);
     cudaMemsetAsync(c.dscal + 8, 0, sizeof(double) * NK0SLOTS, c.stream);
     const int ntiles = (c.N / TILE) * (c.N / TILE) * (c.N / TILE);
-    k_project<T><<<ntiles, DEP_THREADS, dep_smem<T>(), c.stream>>>(p);
+    if (c.dep_shape == 1) {
+        dep_attrs<T, 1>();
+        k_project<T, 1><<<ntiles, DEP_THREADS, dep_smem<T, 1>(), c.stream>>>(p);
+    } else {
+        dep_attrs<T, 0>();
+        k_project<T, 0><<<ntiles, DEP_THREADS, dep_smem<T, 0>(), c.stream>>>(p);
+    }
     k_k0_reduce<<<1, 1024, 0, c.stream>>>(c.dscal);
     c.launches += 2;
 }
 
+// One deposit launch over several boxes of one precision and one deposit shape (batches of MAXBATCH).
 template <class T>
-void launch_kick_drift(Ctx &c, const StepScalars &s)
+void launch_project_batch(Ctx *const *cs, const StepScalars *ss, int n, int shape, cudaStream_t st)
 {
-    static std::atomic<uint64_t> attr{0};
-    if (first_on_device(attr)) {
-        cudaFuncSetAttribute(k_kick_drift<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kd_smem<T>());
+    for (int b0 = 0; b0 < n; b0 += MAXBATCH) {
+        const int nb = std::min(MAXBATCH, n - b0);
+        static DepBatch<T> q;   // host staging of the launch parameters (copied at launch)
+        K0Batch kq{};
+        q.nbox = nb;
+        q.first[0] = 0;
+        for (int i = 0; i < nb; i++) {
+            Ctx &c = *cs[b0 + i];
+            q.box[i] = dep_params<T>(c, ss[b0 + i]);
+            q.first[i + 1] = q.first[i] + (c.N / TILE) * (c.N / TILE) * (c.N / TILE);
+            kq.dscal[i] = c.dscal;
+            cudaMemsetAsync(c.dscal + 8, 0, sizeof(double) * NK0SLOTS, st);
+            c.launches += 2;
+        }
+        if (shape == 1) {
+            dep_attrs<T, 1>();
+            k_project_batch<T, 1><<<q.first[nb], DEP_THREADS, dep_smem<T, 1>(), st>>>(q);
+        } else {
+            dep_attrs<T, 0>();
+            k_project_batch<T, 0><<<q.first[nb], DEP_THREADS, dep_smem<T, 0>(), st>>>(q);
+        }
+        k_k0_reduce_batch<<<nb, 1024, 0, st>>>(kq);
     }
+}
+
+template <class T> KdParams<T> kd_params(const Ctx &c, const StepScalars &s)
+{
     KdParams<T> p{};
     p.part = reinterpret_cast<Particle<T> *>(c.part[c.cur]);
     p.start = c.start;
@@ -942,9 +1039,81 @@ void launch_kick_drift(Ctx &c, const StepScalars &s)
     p.dt_kick = (T)s.dtau_kick;
     p.dt_drift_N = (T)(s.dtau * c.N);
     p.halfN = (T)(0.5 * c.N);
+    return p;
+}
+
+template <class T> void kd_attrs()
+{
+    static std::atomic<uint64_t> attr{0};
+    if (first_on_device(attr)) {
+        cudaFuncSetAttribute(k_kick_drift<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kd_smem<T>());
+        cudaFuncSetAttribute(k_kick_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kd_smem<T>());
+    }
+}
+
+template <class T>
+void launch_kick_drift(Ctx &c, const StepScalars &s)
+{
+    kd_attrs<T>();
+    const KdParams<T> p = kd_params<T>(c, s);
     const int ntiles = (c.N / KT) * (c.N / KT) * (c.N / KT);
     k_kick_drift<T><<<ntiles, KD_THREADS, kd_smem<T>(), c.stream>>>(p);
     c.launches++;
+}
+
+// One gather + kick + drift launch over several boxes of one precision (batches of MAXBATCH).
+template <class T>
+void launch_kick_batch(Ctx *const *cs, const StepScalars *ss, int n, cudaStream_t st)
+{
+    kd_attrs<T>();
+    for (int b0 = 0; b0 < n; b0 += MAXBATCH) {
+        const int nb = std::min(MAXBATCH, n - b0);
+        static KdBatch<T> q;
+        q.nbox = nb;
+        q.first[0] = 0;
+        for (int i = 0; i < nb; i++) {
+            Ctx &c = *cs[b0 + i];
+            q.box[i] = kd_params<T>(c, ss[b0 + i]);
+            q.first[i + 1] = q.first[i] + (c.N / KT) * (c.N / KT) * (c.N / KT);
+            c.launches++;
+        }
+        k_kick_batch<T><<<q.first[nb], KD_THREADS, kd_smem<T>(), st>>>(q);
+    }
+}
+
+// Time the deposit of the context's current state with each chunk capacity and keep the fastest.  The trial
+// deposits write into the spectrum buffer, which holds nothing between steps (9 half spectra hold more than
+// 9 real fields), so the sources the caller can read stay as they were; the k = 0 scalar they also write is
+// recomputed by the next projection before the solve reads it.
+template <class T>
+int tune_deposit_shape(Ctx &c, const StepScalars &s)
+{
+    void *const src = c.src;
+    c.src = c.spec;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_v = 0;
+    for (int v = 0; v < NDEPSHAPES; v++) {
+        c.dep_shape = v;
+        launch_project<T>(c, s);   // warm-up (and the first launch of the shape)
+        cudaEventRecord(e0, c.stream);
+        for (int r = 0; r < 3; r++) launch_project<T>(c, s);
+        cudaEventRecord(e1, c.stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.src = src;
+    c.dep_shape = best_v;
+    return best_v;
 }
 
 void launch_scan(Ctx &c)
@@ -1027,6 +1196,9 @@ void launch_check_finite(Ctx &c, const double *d, int64_t n, int *d_flag)
 
 #define PM_INST(T)                                                                          \
     template void launch_project<T>(Ctx &, const StepScalars &);                            \
+    template void launch_project_batch<T>(Ctx *const *, const StepScalars *, int, int, cudaStream_t); \
+    template void launch_kick_batch<T>(Ctx *const *, const StepScalars *, int, cudaStream_t); \
+    template int tune_deposit_shape<T>(Ctx &, const StepScalars &);                         \
     template void launch_kick_drift<T>(Ctx &, const StepScalars &);                         \
     template void launch_sort<T>(Ctx &);                                                    \
     template void launch_load_particles<T>(Ctx &, const double *, const double *, int64_t,  \

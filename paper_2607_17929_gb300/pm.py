@@ -63,6 +63,9 @@ def _load():
         "pm_get_schedule": ([vp, dp, dp, dp], C.c_int),
         "pm_get_timings": ([vp, dp, C.c_int, C.POINTER(i64)], C.c_int),
         "pm_fft_shapes": ([vp, i32, i32, C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "pm_deposit_shape": ([vp, i32, C.POINTER(i32)], C.c_int),
+        "pm_ensemble_set_batched": ([vp, i32], C.c_int),
+        "pm_ensemble_get_mode": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "pm_put_particles": ([vp, vp, vp], C.c_int),
         "pm_ensemble_init": ([C.c_void_p, i32, C.POINTER(vp)], C.c_int),
         "pm_ensemble_destroy": ([vp], None),
@@ -114,7 +117,8 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_net_set_params", "pm_net_get_params", "pm_net_buffer", "pm_net_features", "pm_net_target",
             "pm_net_forward", "pm_net_backward", "pm_net_adam", "pm_net_train_step", "pm_net_apply",
             "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight", "pm_conv3d_check",
-            "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_fft_shapes", "pm_save", "pm_load"]
+            "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_fft_shapes", "pm_deposit_shape", "pm_save",
+            "pm_load", "pm_ensemble_set_batched", "pm_ensemble_get_mode"]
 
 
 def _ptr(a):
@@ -263,6 +267,14 @@ def pm_fft_shapes(ctx, force_y=-1, force_z=-1):
     return y.value, z.value
 
 
+def pm_deposit_shape(ctx, force=-1):
+    """Select (0, 1), keep (-2) or, with -1, time and keep the faster projection bin shape; returns the shape
+    in use."""
+    v = C.c_int32()
+    _check(ctx, lib.pm_deposit_shape(ctx, int(force), C.byref(v)))
+    return v.value
+
+
 def pm_get_timings(ctx):
     """Mean per-kernel ms over the steps since the previous call, and the kernel launch count."""
     ms = np.zeros(len(TIMINGS))
@@ -334,6 +346,17 @@ def pm_ensemble_stream(e):
 
 def pm_ensemble_set_streams(e, n_streams):
     _echeck(e, lib.pm_ensemble_set_streams(e, int(n_streams)))
+
+
+def pm_ensemble_set_batched(e, batched):
+    _echeck(e, lib.pm_ensemble_set_batched(e, int(bool(batched))))
+
+
+def pm_ensemble_get_mode(e):
+    """(stream count, batched flag) in use."""
+    k, b = C.c_int32(), C.c_int32()
+    _echeck(e, lib.pm_ensemble_get_mode(e, C.byref(k), C.byref(b)))
+    return k.value, bool(b.value)
 
 
 def pm_ensemble_tune(e):

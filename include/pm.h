@@ -174,6 +174,29 @@ pm_status pm_put_particles(pm_ctx *ctx, const double *pos, const double *mom);
  * may be NULL to skip it.  Errors: INVALID_ARG, STATE, CUDA. */
 pm_status pm_get_particles(pm_ctx *ctx, double *pos, double *mom);
 
+/* Particle state in the mixed form's own precision (28 bytes a particle
+ * instead of the 48 of two f64 triples), for I/O across the CPU-GPU link: the
+ * cell index c = i + N (j + N k) of the vertex-centred mesh, the offsets
+ * f in [0, 1) inside the cell (position x = (i + f_x) / N, ...) and the
+ * momentum per unit mass u, as the mixed step stores them (the paper's
+ * mixed-precision positions are cell plus offset; its Sec. 3.1 momentum). */
+typedef struct {
+    int32_t cell;
+    float f[3];
+    float u[3];
+} pm_packed_particle;
+
+/* pm_put_particles / pm_set_particles / pm_get_particles with n_part packed
+ * records (host, pinned host or device memory; pinned and device memory are
+ * read and written by the kernels in place).  Mixed-precision contexts only.
+ * The records are taken as they are: no rounding, ids are the record order.
+ * Errors: INVALID_ARG (NULL, an FP64 context, a cell outside [0, N^3), an
+ * offset outside [0, 1), a non-finite offset or momentum), STATE (put: no
+ * particles yet or mid-step), CUDA. */
+pm_status pm_set_particles_packed(pm_ctx *ctx, const pm_packed_particle *p);
+pm_status pm_put_particles_packed(pm_ctx *ctx, const pm_packed_particle *p);
+pm_status pm_get_particles_packed(pm_ctx *ctx, pm_packed_particle *p);
+
 /* One N^3 real field as f64 (see PM_FIELD_*), [z][y][x].  Errors: INVALID_ARG, STATE, CUDA. */
 pm_status pm_get_field(pm_ctx *ctx, int field_id, double *dst);
 

@@ -256,7 +256,9 @@ void rotate(Ctx &c)
 
 namespace {
 
-template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const double *mom, bool bootstrap)
+template <class T>
+pm_status set_particles_t(Ctx &c, const double *pos, const double *mom, bool bootstrap,
+                          const pm_packed_particle *packed = nullptr)
 {
     if (bootstrap) {
         c.have_particles = false;
@@ -266,7 +268,28 @@ template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const do
     const double *kpos = kernel_ptr(pos), *kmom = kernel_ptr(mom);
     int *dflag = reinterpret_cast<int *>(c.dscal + 4);
     CK(cudaMemsetAsync(dflag, 0, sizeof(int), c.stream));
-    if (kpos && kmom) {
+    if constexpr (sizeof(T) == 4) {
+        if (packed) {
+            const pm_packed_particle *kp = kernel_ptr(packed);
+            if (kp) {
+                launch_load_packed(c, kp, 0, c.np, dflag);   // device or pinned host records, read in place
+                CKL("load_packed");
+            } else {
+                auto *st = reinterpret_cast<pm_packed_particle *>(c.stage_buf);
+                const int64_t chunk = c.stage_elems * (int64_t)sizeof(double) / (int64_t)sizeof(pm_packed_particle);
+                for (int64_t f = 0; f < c.np; f += chunk) {
+                    const int64_t n = std::min(chunk, c.np - f);
+                    CK(cudaMemcpyAsync(st, packed + f, sizeof(pm_packed_particle) * n, cudaMemcpyHostToDevice,
+                                       c.stream));
+                    launch_load_packed(c, st, f, n, dflag);
+                    CKL("load_packed");
+                }
+            }
+        }
+    }
+    if (packed) {
+        // loaded above
+    } else if (kpos && kmom) {
         // device or pinned host arrays: one pass reads them, checks them and builds the records
         launch_load_particles<T>(c, kpos, kmom, 0, c.np, dflag);
         CKL("load");
@@ -287,7 +310,9 @@ template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const do
     CK(cudaStreamSynchronize(c.stream));
     if (hflag) {
         if (!bootstrap) c.have_particles = false;  // the previous state was overwritten
-        return fail(c, PM_ERR_INVALID_ARG, "non-finite position or momentum");
+        return fail(c, PM_ERR_INVALID_ARG, packed ? "packed record with a cell out of range, an offset outside [0, 1) "
+                                                    "or a non-finite value"
+                                                  : "non-finite position or momentum");
     }
     launch_sort<T>(c);
     CKL("sort");
@@ -312,6 +337,29 @@ template <class T> pm_status set_particles_t(Ctx &c, const double *pos, const do
     CK(cudaMemsetAsync(c.chi, 0, sizeof(T) * c.nc, c.stream));
     c.have_particles = true;
     c.stage = 0;
+    return PM_OK;
+}
+
+pm_status get_packed_t(Ctx &c, pm_packed_particle *out)
+{
+    launch_store_particles_scatter<float>(c, nullptr, nullptr);   // records in id order
+    CKL("unpermute");
+    pm_packed_particle *kp = kernel_ptr(out);
+    if (kp) {
+        launch_store_packed(c, kp, 0, c.np);
+        CKL("store_packed");
+        if (!is_device_ptr(out)) CK(cudaStreamSynchronize(c.stream));
+        return PM_OK;
+    }
+    auto *st = reinterpret_cast<pm_packed_particle *>(c.stage_buf);
+    const int64_t chunk = c.stage_elems * (int64_t)sizeof(double) / (int64_t)sizeof(pm_packed_particle);
+    for (int64_t f = 0; f < c.np; f += chunk) {
+        const int64_t n = std::min(chunk, c.np - f);
+        launch_store_packed(c, st, f, n);
+        CKL("store_packed");
+        CK(cudaMemcpyAsync(out + f, st, sizeof(pm_packed_particle) * n, cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
     return PM_OK;
 }
 
@@ -756,6 +804,38 @@ pm_status pm_put_particles(pm_ctx *ctx, const double *pos, const double *mom)
     if (!pos || !mom) return fail(c, PM_ERR_INVALID_ARG, "pm_put_particles: NULL array");
     if (!c.have_particles || c.stage != 0) return fail(c, PM_ERR_STATE, "pm_put_particles: not between steps");
     return PM_DISPATCH(ctx, set_particles_t, c, pos, mom, false);
+}
+
+pm_status pm_set_particles_packed(pm_ctx *ctx, const pm_packed_particle *p)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (!p) return fail(c, PM_ERR_INVALID_ARG, "pm_set_particles_packed: NULL array");
+    if (!c.mixed) return fail(c, PM_ERR_INVALID_ARG, "pm_set_particles_packed: packed records need a mixed context");
+    return set_particles_t<float>(c, nullptr, nullptr, true, p);
+}
+
+pm_status pm_put_particles_packed(pm_ctx *ctx, const pm_packed_particle *p)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (!p) return fail(c, PM_ERR_INVALID_ARG, "pm_put_particles_packed: NULL array");
+    if (!c.mixed) return fail(c, PM_ERR_INVALID_ARG, "pm_put_particles_packed: packed records need a mixed context");
+    if (!c.have_particles || c.stage != 0) return fail(c, PM_ERR_STATE, "pm_put_particles_packed: not between steps");
+    return set_particles_t<float>(c, nullptr, nullptr, false, p);
+}
+
+pm_status pm_get_particles_packed(pm_ctx *ctx, pm_packed_particle *p)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (!p) return fail(c, PM_ERR_INVALID_ARG, "pm_get_particles_packed: NULL array");
+    if (!c.mixed) return fail(c, PM_ERR_INVALID_ARG, "pm_get_particles_packed: packed records need a mixed context");
+    if (!c.have_particles) return fail(c, PM_ERR_STATE, "pm_get_particles_packed: no particles");
+    return get_packed_t(c, p);
 }
 
 pm_status pm_project(pm_ctx *ctx)

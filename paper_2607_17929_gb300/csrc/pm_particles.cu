@@ -823,6 +823,76 @@ __global__ void k_load(const double *pos, const double *mom, int64_t first, int6
     atomicAdd(&count[P.cell], 1);
 }
 
+// Packed host records (cell, 3 f32 offsets, 3 f32 momenta; 28 bytes) -> device records, checked.  A block
+// takes PK_P records (14336 bytes) and moves them between the caller's array and shared memory with 16-byte
+// accesses at consecutive addresses (the array may be pinned host memory read across the CPU-GPU link, where
+// narrow accesses waste most of each transfer); vec = 0 (an array not 16-byte aligned) uses 4-byte accesses.
+constexpr int PK_P = 512;
+constexpr int PK_VEC = PK_P * (int)sizeof(pm_packed_particle) / 16;
+static_assert(sizeof(pm_packed_particle) == 28 && PK_P * 28 % 16 == 0, "packed record");
+
+__device__ __forceinline__ void pk_copy(uint4 *dst, const uint4 *src, int bytes, int vec)
+{
+    const int nv = vec ? bytes / 16 : 0;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) dst[v] = src[v];
+    for (int w = nv * 4 + threadIdx.x; w < bytes / 4; w += blockDim.x)
+        reinterpret_cast<uint32_t *>(dst)[w] = reinterpret_cast<const uint32_t *>(src)[w];
+}
+
+__global__ void __launch_bounds__(256) k_load_packed(const pm_packed_particle *in, int64_t first, int64_t cnt,
+                                                     int64_t nc, Particle<float> *out, int32_t *count, int *bad, int vec)
+{
+    __shared__ uint4 sb[PK_VEC];
+    const int64_t base = (int64_t)blockIdx.x * PK_P;
+    const int nb = (int)min((int64_t)PK_P, cnt - base);
+    pk_copy(sb, reinterpret_cast<const uint4 *>(in + base), nb * 28, vec);
+    __syncthreads();
+    const pm_packed_particle *sq = reinterpret_cast<const pm_packed_particle *>(sb);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const pm_packed_particle q = sq[j];
+        Particle<float> P;
+        P.cell = q.cell;
+        P.id = (uint32_t)(first + base + j);
+        bool ok = q.cell >= 0 && (int64_t)q.cell < nc;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            P.f[d] = q.f[d];
+            P.u[d] = q.u[d];
+            ok = ok && q.f[d] >= 0.f && q.f[d] < 1.f && isfinite(q.u[d]);
+        }
+        if (!ok) {   // keeps the cell index valid; the caller rejects the input
+            *bad = 1;
+            P.cell = 0;
+            P.f[0] = P.f[1] = P.f[2] = 0.f;
+        }
+        out[first + base + j] = P;
+        atomicAdd(&count[P.cell], 1);
+    }
+}
+
+// Device records in id order -> packed records (same staging as the load).
+__global__ void __launch_bounds__(256) k_store_packed(const Particle<float> *byid, int64_t first, int64_t cnt,
+                                                      pm_packed_particle *out, int vec)
+{
+    __shared__ uint4 sb[PK_VEC];
+    const int64_t base = (int64_t)blockIdx.x * PK_P;
+    const int nb = (int)min((int64_t)PK_P, cnt - base);
+    pm_packed_particle *sq = reinterpret_cast<pm_packed_particle *>(sb);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const Particle<float> P = byid[first + base + j];
+        pm_packed_particle q;
+        q.cell = P.cell;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            q.f[d] = P.f[d];
+            q.u[d] = P.u[d];
+        }
+        sq[j] = q;
+    }
+    __syncthreads();
+    pk_copy(reinterpret_cast<uint4 *>(out + base), sb, nb * 28, vec);
+}
+
 template <class T>
 __global__ void k_unpermute(const Particle<T> *in, Particle<T> *out, int64_t np)
 {
@@ -1163,6 +1233,21 @@ void launch_store_particles(Ctx &c, double *d_pos, double *d_mom, int64_t first,
     const int vec = ((reinterpret_cast<uintptr_t>(d_pos) | reinterpret_cast<uintptr_t>(d_mom)) & 15) == 0;
     k_store<T><<<nblk(count, ST_P), 256, 0, c.stream>>>(reinterpret_cast<const Particle<T> *>(c.part[o]), first,
                                                         count, c.N, 1.0 / (double)c.N, d_pos, d_mom, vec);
+}
+
+void launch_load_packed(Ctx &c, const pm_packed_particle *in, int64_t first, int64_t count, int *d_bad)
+{
+    const int vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    k_load_packed<<<nblk(count, PK_P), 256, 0, c.stream>>>(in, first, count, c.nc,
+                                                           reinterpret_cast<Particle<float> *>(c.part[c.cur]), c.count,
+                                                           d_bad, vec);
+}
+
+void launch_store_packed(Ctx &c, pm_packed_particle *out, int64_t first, int64_t count)
+{
+    const int vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    k_store_packed<<<nblk(count, PK_P), 256, 0, c.stream>>>(
+        reinterpret_cast<const Particle<float> *>(c.part[1 - c.cur]), first, count, out, vec);
 }
 
 template <class T>

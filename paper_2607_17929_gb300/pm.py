@@ -64,6 +64,9 @@ def _load():
         "pm_get_timings": ([vp, dp, C.c_int, C.POINTER(i64)], C.c_int),
         "pm_fft_shapes": ([vp, i32, i32, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "pm_deposit_shape": ([vp, i32, C.POINTER(i32)], C.c_int),
+        "pm_set_particles_packed": ([vp, vp], C.c_int),
+        "pm_put_particles_packed": ([vp, vp], C.c_int),
+        "pm_get_particles_packed": ([vp, vp], C.c_int),
         "pm_ensemble_set_batched": ([vp, i32], C.c_int),
         "pm_ensemble_get_mode": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "pm_put_particles": ([vp, vp, vp], C.c_int),
@@ -118,7 +121,8 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_net_forward", "pm_net_backward", "pm_net_adam", "pm_net_train_step", "pm_net_apply",
             "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight", "pm_conv3d_check",
             "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_fft_shapes", "pm_deposit_shape", "pm_save",
-            "pm_load", "pm_ensemble_set_batched", "pm_ensemble_get_mode"]
+            "pm_load", "pm_ensemble_set_batched", "pm_ensemble_get_mode", "pm_set_particles_packed",
+            "pm_put_particles_packed", "pm_get_particles_packed"]
 
 
 def _ptr(a):
@@ -265,6 +269,34 @@ def pm_fft_shapes(ctx, force_y=-1, force_z=-1):
     y, z = C.c_int32(), C.c_int32()
     _check(ctx, lib.pm_fft_shapes(ctx, force_y, force_z, C.byref(y), C.byref(z)))
     return y.value, z.value
+
+
+# pm_packed_particle: int32 cell, 3 f32 offsets in [0, 1), 3 f32 momenta (28 bytes)
+PACKED = np.dtype([("cell", "<i4"), ("f", "<f4", (3,)), ("u", "<f4", (3,))])
+assert PACKED.itemsize == 28
+
+
+def _packed_ptr(a, n):
+    """Pointer to n packed records: a numpy array of dtype PACKED or a torch uint8 tensor of 28 n bytes."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != PACKED or a.size != n or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"packed particles must be a contiguous array of {n} records of dtype PACKED")
+        return a.ctypes.data
+    if getattr(a, "numel", None) is None or a.numel() * a.element_size() != 28 * n or not a.is_contiguous():
+        raise ValueError(f"packed particles must be a contiguous tensor of {28 * n} bytes")
+    return a.data_ptr()
+
+
+def pm_set_particles_packed(ctx, n_part, records):
+    _check(ctx, lib.pm_set_particles_packed(ctx, _packed_ptr(records, n_part)))
+
+
+def pm_put_particles_packed(ctx, n_part, records):
+    _check(ctx, lib.pm_put_particles_packed(ctx, _packed_ptr(records, n_part)))
+
+
+def pm_get_particles_packed(ctx, n_part, records):
+    _check(ctx, lib.pm_get_particles_packed(ctx, _packed_ptr(records, n_part)))
 
 
 def pm_deposit_shape(ctx, force=-1):

@@ -280,3 +280,60 @@ def test_mixed_precision_tuned_fft_sizes(pm, n, n_side, box, newtonian):
     print(f"mixed {n}^3 vs oracle:", {k: f"{v:.2e}" for k, v in e.items()}, f"rms dx {rms_cells:.2e} cell")
     assert not mixed_violations(e), mixed_violations(e)
     assert rms_cells < 1e-6, rms_cells
+
+
+def test_packed_particle_io(pm):
+    """Packed records (int32 cell, f32 offsets, f32 momenta: the mixed form's own precision) in and out:
+    they reproduce the f64 view exactly, a context started from them steps like one started from f64,
+    pinned host records are read and written in place, and invalid records or an FP64 context are refused."""
+    import torch
+    n, box = 16, 160.0
+    orc = O.OracleSim(n, n ** 3, OM, box, 100.0, 0.0, 100)
+    pos, mom = ics.zeldovich_ics(n, box, OM, H, orc.a_n[0], orc.a_n[0], 12)
+    a = pm.PM(n, n ** 3, box, OM, 100.0, 0.0, 100, pm.PM_MIXED)
+    a.set_particles(pos, mom)
+    rec = np.zeros(n ** 3, dtype=pm.PACKED)
+    pm.pm_get_particles_packed(a.ctx, n ** 3, rec)
+    pa, ua = a.particles()
+    c = rec["cell"].astype(np.int64)
+    ijk = np.stack([c % n, (c // n) % n, c // (n * n)], axis=1)
+    assert np.array_equal((ijk + rec["f"].astype(np.float64)) * (1.0 / n), pa)
+    assert np.array_equal(rec["u"].astype(np.float64), ua)
+    assert np.all((rec["f"] >= 0) & (rec["f"] < 1))
+    # a context started from the records steps like the one started from f64
+    b = pm.PM(n, n ** 3, box, OM, 100.0, 0.0, 100, pm.PM_MIXED)
+    pm.pm_set_particles_packed(b.ctx, n ** 3, rec)
+    for _ in range(2):
+        a.step(); b.step()
+    pa, ua = a.particles()
+    pb, ub = b.particles()
+    assert np.sqrt(np.mean(wrapdiff(pa, pb) ** 2)) * n < 1e-6 and rel(ub, ua) < 1e-5
+    # pinned host records, in place, both directions, match the device-array path
+    hrec = torch.from_numpy(rec.view(np.uint8).copy()).pin_memory()
+    drec = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+    pm.pm_put_particles_packed(a.ctx, n ** 3, hrec)
+    pm.pm_put_particles_packed(b.ctx, n ** 3, drec)
+    a.step(); b.step()
+    hout = torch.zeros(28 * n ** 3, dtype=torch.uint8).pin_memory()
+    dout = torch.zeros(28 * n ** 3, dtype=torch.uint8, device="cuda")
+    pm.pm_get_particles_packed(a.ctx, n ** 3, hout)
+    pm.pm_get_particles_packed(b.ctx, n ** 3, dout)
+    torch.cuda.synchronize()
+    ra = hout.numpy().view(pm.PACKED)
+    rb = dout.cpu().numpy().view(pm.PACKED)
+    assert np.array_equal(ra["cell"], rb["cell"])
+    assert np.max(np.abs(ra["f"] - rb["f"])) < 1e-5 and np.max(np.abs(ra["u"] - rb["u"])) < 1e-6 * np.abs(rb["u"]).max()
+    # invalid records are refused
+    for field, idx, value in (("f", (3, 1), 1.0), ("cell", 7, n ** 3), ("u", (5, 2), np.nan), ("f", (0, 0), -1e-8)):
+        bad = rec.copy()
+        bad[field][idx] = value
+        with pytest.raises(pm.PMError) as ei:
+            pm.pm_put_particles_packed(a.ctx, n ** 3, bad)
+        assert ei.value.status == pm.PM_ERR_INVALID_ARG
+        pm.pm_set_particles_packed(a.ctx, n ** 3, rec)   # the refused put left no valid state; start again
+    a.close(); b.close()
+    g = pm.PM(n, n ** 3, box, OM, 100.0, 0.0, 100, pm.PM_FP64)
+    with pytest.raises(pm.PMError) as ei:
+        pm.pm_set_particles_packed(g.ctx, n ** 3, rec)
+    assert ei.value.status == pm.PM_ERR_INVALID_ARG
+    g.close()

@@ -446,12 +446,19 @@ k_c2r_fast(const __grid_constant__ Ptrs in, const __grid_constant__ Ptrs out, co
     T *dst = reinterpret_cast<T *>(out.p[blockIdx.y]);
     const fftc::RowIdx<N> ix{l * fftc::RowIdx<N>::pitch};
     const C *ia = src + 2 * pair * H, *ib = ia + H;
-    for (int k = t; k < H; k += G::TL) {
-        C A = fftc::mk<C>(0, 0), B = fftc::mk<C>(0, 0);
-        if (ok) {
-            A = ia[k];
-            B = ib[k];
-        }
+    constexpr int NK = (H + G::TL - 1) / G::TL;
+    C As[NK], Bs[NK];
+#pragma unroll
+    for (int q = 0; q < NK; q++) {
+        const int k = t + q * G::TL;
+        As[q] = (ok && k < H) ? ia[k] : fftc::mk<C>(0, 0);
+        Bs[q] = (ok && k < H) ? ib[k] : fftc::mk<C>(0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < NK; q++) {
+        const int k = t + q * G::TL;
+        if (k >= H) break;
+        C A = As[q], B = Bs[q];
         if (k == 0 || 2 * k == N) {
             A.y = 0;
             B.y = 0;

@@ -213,28 +213,50 @@ __device__ __forceinline__ void deposit_tile(const DepParams<T> &p, const int b)
     __syncthreads();
 
     // potentials of the previous solve on the 10^3 vertices [x0-1, x0+8]
+    constexpr int NIT = (NFLD + DEP_THREADS - 1) / DEP_THREADS;
+    constexpr int RIT = (NREG + DEP_THREADS - 1) / DEP_THREADS;
+    T a[NIT], c[NIT];
+    int gs0[RIT], gs1[RIT];
     if (p.use_fields) {
-        for (int i = tid; i < NFLD; i += DEP_THREADS) {
-            const int row = i / FLD, rx = i - row * FLD;
-            const int64_t g = (int64_t)rowb[row] + xw[rx];
-            sphi[i] = p.phi1[g];
-            schi[i] = p.chi1[g];
-        }
-    } else {
-        for (int i = tid; i < NFLD; i += DEP_THREADS) {
-            sphi[i] = T(0);
-            schi[i] = T(0);
+#pragma unroll
+        for (int q = 0; q < NIT; q++) {
+            const int i = tid + q * DEP_THREADS;
+            if (i < NFLD) {
+                const int row = i / FLD, rx = i - row * FLD;
+                const int64_t g = (int64_t)rowb[row] + xw[rx];
+                a[q] = p.phi1[g];
+                c[q] = p.chi1[g];
+            }
         }
     }
     // particle ranges of the 9^3 source cells [x0-1, x0+8)
-    for (int i = tid; i < NREG; i += DEP_THREADS) {
-        const int row = i / REG, sx = i - row * REG;
-        const int sy = row % REG, sz = row / REG;
-        const int64_t g = (int64_t)rowb[sy + FLD * sz] + xw[sx];
-        int gs = p.start[g];
-        scnt[i] = p.start[g + 1] - gs;
-        soff[i] = scnt[i];
-        sgs[i] = gs;
+#pragma unroll
+    for (int q = 0; q < RIT; q++) {
+        const int i = tid + q * DEP_THREADS;
+        if (i < NREG) {
+            const int row = i / REG, sx = i - row * REG;
+            const int sy = row % REG, sz = row / REG;
+            const int64_t g = (int64_t)rowb[sy + FLD * sz] + xw[sx];
+            gs0[q] = p.start[g];
+            gs1[q] = p.start[g + 1];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NIT; q++) {
+        const int i = tid + q * DEP_THREADS;
+        if (i < NFLD) {
+            sphi[i] = p.use_fields ? a[q] : T(0);
+            schi[i] = p.use_fields ? c[q] : T(0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RIT; q++) {
+        const int i = tid + q * DEP_THREADS;
+        if (i < NREG) {
+            scnt[i] = gs1[q] - gs0[q];
+            soff[i] = gs1[q] - gs0[q];
+            sgs[i] = gs0[q];
+        }
     }
     __syncthreads();
     const int total = block_exclusive_scan(soff, NREG, wtmp);
@@ -249,15 +271,23 @@ __device__ __forceinline__ void deposit_tile(const DepParams<T> &p, const int b)
 
     for (int lo = 0; lo < total; lo += CAP) {
         const int hi = min(total, lo + CAP);
-        for (int i = lo + tid; i < hi; i += DEP_THREADS) {
-            // source cell of local particle i: largest t with soff[t] <= i
+        // source cell of local particle i: largest t with soff[t] <= i
+        auto cell_of = [&](int i) {
             int t0 = 0, t1 = NREG - 1;
             while (t0 < t1) {
                 int m = (t0 + t1 + 1) >> 1;
                 if (soff[m] <= i) t0 = m;
                 else t1 = m - 1;
             }
-            const int t = t0;
+            return t0;
+        };
+        int tn = lo + tid < hi ? cell_of(lo + tid) : 0;
+        for (int i = lo + tid; i < hi; i += DEP_THREADS) {
+            const int t = tn;
+            if (i + DEP_THREADS < hi) {   // the next particle of this thread: its cell now, its record into L1
+                tn = cell_of(i + DEP_THREADS);
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(p.part + sgs[tn] + (i + DEP_THREADS - soff[tn])));
+            }
             const Particle<T> P = p.part[sgs[t] + (i - soff[t])];
             const int sx = t % REG, sy = (t / REG) % REG, sz = t / (REG * REG);
             DepRec<T> r;
@@ -566,19 +596,39 @@ __device__ __forceinline__ void kick_tile(const KdParams<T> &p, const int b)
         if (tid < KT * KT) roff[tid] = x - cnt + (wid == 1 ? wtmp[0] : 0);
         if (tid == 0) roff[KT * KT] = wtmp[0] + wtmp[1];
     }
-    // fields on the vertex block
-    for (int i = tid; i < KNV; i += KD_THREADS) {
-        const int row = i / KV, rx = i - row * KV;
-        const int64_t g = (int64_t)rowb[row] + xw[rx];
-        Vtx4<T> a;
-        a.phi = __ldg(p.phi + g);
-        if (!p.newtonian) {
-            a.chi = __ldg(p.chi + g);
-            a.bx = __ldg(p.Bx + g);
-            a.by = __ldg(p.By + g);
-            sbz[i] = __ldg(p.Bz + g);
+    // fields on the vertex block: every load of this thread's vertices issued before the stores
+    if (p.newtonian) {
+        for (int i = tid; i < KNV; i += KD_THREADS) {
+            const int row = i / KV, rx = i - row * KV;
+            Vtx4<T> a;
+            a.phi = __ldg(p.phi + (int64_t)rowb[row] + xw[rx]);
+            sv[i] = a;
         }
-        sv[i] = a;
+    } else {
+        constexpr int KIT = (KNV + KD_THREADS - 1) / KD_THREADS;
+        Vtx4<T> va[KIT];
+        T vz[KIT];
+#pragma unroll
+        for (int q = 0; q < KIT; q++) {
+            const int i = tid + q * KD_THREADS;
+            if (i < KNV) {
+                const int row = i / KV, rx = i - row * KV;
+                const int64_t g = (int64_t)rowb[row] + xw[rx];
+                va[q].phi = __ldg(p.phi + g);
+                va[q].chi = __ldg(p.chi + g);
+                va[q].bx = __ldg(p.Bx + g);
+                va[q].by = __ldg(p.By + g);
+                vz[q] = __ldg(p.Bz + g);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < KIT; q++) {
+            const int i = tid + q * KD_THREADS;
+            if (i < KNV) {
+                sv[i] = va[q];
+                sbz[i] = vz[q];
+            }
+        }
     }
     __syncthreads();
     const int total = roff[KT * KT];

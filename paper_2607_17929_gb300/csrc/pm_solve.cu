@@ -55,6 +55,20 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
     C *S = reinterpret_cast<C *>(p.spec);
     C *H = reinterpret_cast<C *>(p.tens);
     const int64_t nh = p.nh;
+    // every input of this mode, loaded before any output is stored
+    const bool fullmode = p.full && !zero && !nyq;
+    const bool bint = p.b_space && !p.b_seed;
+    C inR, inS[5], inH[4], inF[3];
+    if (!zero) inR = S[e];
+    if (fullmode) {
+#pragma unroll
+        for (int c = 0; c < 5; c++) inS[c] = S[(4 + c) * nh + e];
+#pragma unroll
+        for (int c = 0; c < 4; c++) inH[c] = H[c * nh + e];
+        const C *FB = bint ? reinterpret_cast<const C *>(p.bstate) : S + nh;
+#pragma unroll
+        for (int c = 0; c < 3; c++) inF[c] = FB[c * nh + e];
+    }
 
     // scalar potential phi
     if (zero) {
@@ -70,7 +84,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
         v.y = 0;
         S[0] = v;
     } else {
-        C R = S[e];
+        C R = inR;
         const T f = -p.inv_n3 / (k2 + p.cphi);
         R.x *= f;
         R.y *= f;
@@ -93,8 +107,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
         return;
     }
     // trace-free Sig as a symmetric matrix (Sig_zz = -Sig_xx - Sig_yy)
-    const C sxx = S[4 * nh + e], sxy = S[5 * nh + e], sxz = S[6 * nh + e], syy = S[7 * nh + e],
-            syz = S[8 * nh + e];
+    const C sxx = inS[0], sxy = inS[1], sxz = inS[2], syy = inS[3], syz = inS[4];
     C szz;
     szz.x = -sxx.x - syy.x;
     szz.y = -sxx.y - syy.y;
@@ -136,7 +149,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
 #pragma unroll
         for (int a = 0; a < 2; a++) {
             const C s = a == 0 ? sp : sx;
-            C hh = H[a * nh + e], vv = H[(2 + a) * nh + e];
+            C hh = inH[a], vv = inH[2 + a];
             C r1, r2;
             r1.x = hh.x + p12 * vv.x;
             r1.y = hh.y + p12 * vv.y;
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
         for (int j = 0; j < 3; j++) {
             // dtau W_j = dtau (-i) (v_j - kt_j kv / kt^2) / kt^2
             const T px = v[j].x - kt[j] * kv.x * ik2, py = v[j].y - kt[j] * kv.y * ik2;
-            C b = BS[j * nh + e];
+            C b = inF[j];
             b.x = p.b_decay * b.x + w * py;
             b.y = p.b_decay * b.y - w * px;
             BS[j * nh + e] = b;
@@ -194,7 +207,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveParams<T> p)
             S[(1 + j) * nh + e] = b;
         }
     } else {
-        const C F[3] = {S[nh + e], S[2 * nh + e], S[3 * nh + e]};
+        const C F[3] = {inF[0], inF[1], inF[2]};
         C kF;
         kF.x = kt[0] * F[0].x + kt[1] * F[1].x + kt[2] * F[2].x;
         kF.y = kt[0] * F[0].y + kt[1] * F[1].y + kt[2] * F[2].y;

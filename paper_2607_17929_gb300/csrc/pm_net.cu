@@ -230,18 +230,28 @@ __device__ __forceinline__ void tc_load_halo(uint32_t buf, const uint4 *x, int n
     asm volatile("cp.async.commit_group;");
 }
 
-// read the 4 M blocks of accumulator `acc` (TMEM column offset) back, add bias, activate, store
-template <bool RELU, bool OUTF32>
+// read the 4 M blocks of accumulator `acc` (TMEM column offset) back, add bias, activate, store.  MASK (BF16
+// output only): zero every output channel whose value in mact ([cell][16] BF16) is not positive, the ReLU
+// derivative of a layer whose output mact is, and add the stored values to part[channel].
+template <bool RELU, bool OUTF32, bool MASK>
 __device__ __forceinline__ void tc_epilogue(uint32_t tmem, uint32_t acc, const float *bias, void *y, int n, int tile,
-                                            bool ok)
+                                            bool ok, const uint4 *mact, float (&part)[16])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int x0, y0, z0;
     tc_tile_origin(tile, n, x0, y0, z0);
     // TMEM lane 32 warp + lane = M row m = cx + 8 cy of every z-plane block t (columns 16 t .. 16 t + 15)
     const int m = 32 * warp + lane, cx = m & 7, cy = m >> 3;
-#pragma unroll 1
-    for (int t = 0; t < TCZ; t++) {
+    uint4 mk[MASK ? TCZ : 1][2];   // the mask cells of all z-planes, loaded before the accumulator is read
+    if constexpr (MASK) {
+#pragma unroll
+        for (int t = 0; t < TCZ; t++) {
+            const int64_t cell = ((int64_t)(z0 + t) * n + (y0 + cy)) * n + (x0 + cx);
+            mk[t][0] = mact[2 * cell];
+            mk[t][1] = mact[2 * cell + 1];
+        }
+    }
+    auto plane = [&](const int t) {
         uint32_t r[16] = {};
         if (ok) {   // warp-uniform: after a timeout the accumulator is not read
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -268,19 +278,41 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, uint32_t acc, const f
             __nv_bfloat162 *ob = reinterpret_cast<__nv_bfloat162 *>(o);
 #pragma unroll
             for (int c = 0; c < 8; c++) ob[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+            if constexpr (MASK) {
+                const uint4 m0 = mk[t][0], m1 = mk[t][1];
+                const unsigned mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+                unsigned *ow = reinterpret_cast<unsigned *>(o);
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const bool lo = __uint_as_float(mw[k] << 16) > 0.f, hi = __uint_as_float(mw[k] & 0xffff0000u) > 0.f;
+                    ow[k] &= (lo ? 0x0000ffffu : 0u) | (hi ? 0xffff0000u : 0u);
+                    part[2 * k] += __uint_as_float(ow[k] << 16);
+                    part[2 * k + 1] += __uint_as_float(ow[k] & 0xffff0000u);
+                }
+            }
             uint4 *dst = reinterpret_cast<uint4 *>(y) + 2 * cell;
             dst[0] = o[0];
             dst[1] = o[1];
         }
+    };
+    // unrolled for the BF16 outputs (the mask registers need static indices); the FP32 output layer runs
+    // faster rolled
+    if constexpr (OUTF32) {
+#pragma unroll 1
+        for (int t = 0; t < TCZ; t++) plane(t);
+    } else {
+#pragma unroll
+        for (int t = 0; t < TCZ; t++) plane(t);
     }
 }
 
-template <bool RELU, bool OUTF32>
+template <bool RELU, bool OUTF32, bool MASK>
 __global__ void __launch_bounds__(TC_THREADS)
     k_conv_tc(const uint4 *__restrict__ x, const uint4 *__restrict__ w, const float *__restrict__ bias, void *y, int n,
-              int ntiles, int skip_mma)
+              int ntiles, int skip_mma, const uint4 *__restrict__ mact, float *db)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    float part[16] = {};   // MASK: this thread's sums of the stored values per channel
     const uint32_t sbase = smem_u32(smem);
     const uint32_t mbar0 = sbase, tslot = sbase + 16;   // mbarriers at +0 and +8
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -355,7 +387,7 @@ __global__ void __launch_bounds__(TC_THREADS)
         // 4. the next tile's halo into the free buffer (none after a timeout: the buffer may still be read)
         if (ok && tile + step < ntiles) tc_load_halo(sbase + TC_A + (1 - j) * TC_HALO, x, n, tile + step);
         // 5. the previous tile's results
-        if (k > 0) tc_epilogue<RELU, OUTF32>(tmem, 64 * (1 - j), bias, y, n, tile - step, ok);
+        if (k > 0) tc_epilogue<RELU, OUTF32, MASK>(tmem, 64 * (1 - j), bias, y, n, tile - step, ok, mact, part);
     }
     if (k > 0) {
         const int last = first + (k - 1) * step, j = (k - 1) & 1;
@@ -370,7 +402,24 @@ __global__ void __launch_bounds__(TC_THREADS)
             ok = __all_sync(0xffffffffu, ok) != 0;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        tc_epilogue<RELU, OUTF32>(tmem, 64 * j, bias, y, n, last, ok);
+        tc_epilogue<RELU, OUTF32, MASK>(tmem, 64 * j, bias, y, n, last, ok, mact, part);
+    }
+    if constexpr (MASK) {
+        // db[c] += the CTA's sum of part[c]
+        __shared__ float red[TC_THREADS / 32][16];
+#pragma unroll
+        for (int c = 0; c < 16; c++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_xor_sync(0xffffffffu, part[c], o);
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int c = 0; c < 16; c++) red[warp][c] = part[c];
+        __syncthreads();
+        if (tid < 16) {
+            float t = 0.f;
+            for (int w2 = 0; w2 < TC_THREADS / 32; w2++) t += red[w2][tid];
+            atomicAdd(&db[tid], t);
+        }
     }
     asm volatile("cp.async.wait_group 0;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -460,45 +509,91 @@ __global__ void __launch_bounds__(CONV_THREADS, 3)
 }
 
 // dw[d][co][ci] += sum_cells g[cell][co] x[cell + d][ci]; persistent CTAs over 8^3 tiles.
-// Warp w owns the offsets d = w, w + 8, w + 16 (and w + 24 for w < 3).
-__global__ void __launch_bounds__(CONV_THREADS, 2)
+// Warp w of DW_WARPS owns the offsets d = w, w + DW_WARPS, ...  Two shared-memory buffers,
+// each one tile's 10^3 input halo and 8^3 gradient block: cp.async fetches tile k + 1 into one
+// while the warps run tile k's MMAs from the other.
+constexpr int DW_WARPS = 8;
+constexpr int DW_OFFS = (NOFF + DW_WARPS - 1) / DW_WARPS;   // offsets per warp (at most)
+constexpr int DW_HALO = 2 * NH;                        // uint4 per buffer: input halo
+constexpr int DW_BUF = DW_HALO + 2 * TT * TT * TT;     // + gradient block
+constexpr size_t DW_SMEM = 2 * DW_BUF * sizeof(uint4);  // 96768 bytes
+
+__device__ __forceinline__ void cp_async16(void *s, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(s)), "l"(g));
+}
+
+// one tile's halo of x and gradient block into buffer sb.  Halo cell h = (hz HT + hy) HT + hx keeps its
+// 16-byte half q at uint4 2 h + (q ^ bit 2 of hx): the 8 cells of one x-row that an ldmatrix reads then
+// fall in distinct banks, and the swizzle of a shifted operand does not change from one k-step to the
+// next.  The gradient block uses swz (row = tile cell).
+__device__ __forceinline__ int dw_hswz(int h, int hx, int q) { return 2 * h + (q ^ ((hx >> 2) & 1)); }
+
+__device__ __forceinline__ void dw_fetch(uint4 *sb, const uint4 *x, const uint4 *gr, int n, int nt, int tile)
+{
+    const int x0 = (tile % nt) * TT, y0 = ((tile / nt) % nt) * TT, z0 = (tile / (nt * nt)) * TT;
+    for (int i = threadIdx.x; i < 2 * NH; i += blockDim.x) {
+        const int h = i >> 1, q = i & 1;
+        const int hx = h % HT, hy = (h / HT) % HT, hz = h / (HT * HT);
+        const int64_t g = ((int64_t)wrapn(z0 - 1 + hz, n) * n + wrapn(y0 - 1 + hy, n)) * n + wrapn(x0 - 1 + hx, n);
+        cp_async16(&sb[dw_hswz(h, hx, q)], &x[2 * g + q]);
+    }
+    uint4 *sg = sb + DW_HALO;
+    for (int i = threadIdx.x; i < 2 * TT * TT * TT; i += blockDim.x) {
+        const int m = i >> 1, q = i & 1;
+        const int cx = m & 7, cy = (m >> 3) & 7, cz = m >> 6;
+        const int64_t gc = ((int64_t)(z0 + cz) * n + (y0 + cy)) * n + (x0 + cx);
+        cp_async16(&sg[swz(m, q)], &gr[2 * gc + q]);
+    }
+    asm volatile("cp.async.commit_group;");
+}
+
+__global__ void __launch_bounds__(32 * DW_WARPS, 2)
     k_conv_dw(const uint4 *__restrict__ x, const uint4 *__restrict__ gr, float *dw, int n)
 {
-    __shared__ uint4 sx[2 * NH];          // 32000 B
-    __shared__ uint4 sg[2 * TT * TT * TT];  // 16384 B
+    extern __shared__ uint4 dsm[];   // 2 x DW_BUF
     const int nt = n / TT, ntiles = nt * nt * nt;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float acc[4][2][4] = {};
+    float acc[DW_OFFS][2][4] = {};
     // ldmatrix.trans lane roles.  G (A operand, rows = cells, chunk = co half): matrix mi = lane / 8
     // covers cells (mi / 2) * 8 + lane % 8 of the k16 step, chunk mi % 2.
     const int ga_cell = ((lane >> 4) << 3) + (lane & 7), ga_ch = (lane >> 3) & 1;
     // X (B operand): cells ((lane / 8) % 2) * 8 + lane % 8, chunk (lane / 16) = n8 block.
     const int xb_cell = (((lane >> 3) & 1) << 3) + (lane & 7), xb_ch = lane >> 4;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = (tile % nt) * TT, y0 = ((tile / nt) % nt) * TT, z0 = (tile / (nt * nt)) * TT;
-        __syncthreads();
-        load_halo(sx, x, n, x0, y0, z0);
-        for (int i = threadIdx.x; i < 2 * TT * TT * TT; i += blockDim.x) {
-            const int m = i >> 1, q = i & 1;
-            const int cx = m & 7, cy = (m >> 3) & 7, cz = m >> 6;
-            const int64_t gc = ((int64_t)(z0 + cz) * n + (y0 + cy)) * n + (x0 + cx);
-            sg[swz(m, q)] = gr[2 * gc + q];
+    // k-step s covers tile cells 16 s .. 16 s + 15: z = s / 4, y = 2 (s % 4) + k / 8, x = k % 8.  The byte
+    // address of every operand row is a per-lane (and per-offset) base plus a multiple of s known at
+    // compile time (the swizzle bits do not depend on s): 512 s for G, 3200 (s / 4) + 640 (s % 4) for X.
+    const uint32_t ga_off = 16u * swz(ga_cell, ga_ch);
+    uint32_t xb_off[DW_OFFS];
+#pragma unroll
+    for (int o = 0; o < DW_OFFS; o++) {
+        const int d = min(warp + DW_WARPS * o, NOFF - 1);
+        const int dz = d / 9 - 1, dy = (d / 3) % 3 - 1, dx = d % 3 - 1;
+        const int hx = (xb_cell & 7) + dx + 1;
+        const int h = ((dz + 1) * HT + (xb_cell >> 3) + dy + 1) * HT + hx;
+        xb_off[o] = 16u * dw_hswz(h, hx, xb_ch);
+    }
+    if ((int)blockIdx.x < ntiles) dw_fetch(dsm, x, gr, n, nt, blockIdx.x);
+    int b = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, b ^= 1) {
+        // buffer b ^ 1 was last read before the barrier that ended the previous iteration
+        if (tile + (int)gridDim.x < ntiles) {
+            dw_fetch(dsm + (b ^ 1) * DW_BUF, x, gr, n, nt, tile + gridDim.x);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-#pragma unroll 1
-        for (int s = 0; s < 32; s++) {
-            // k16 step s: tile cells m = 16 s + k, i.e. cz = s / 4, cy = 2 (s % 4) + k / 8, cx = k % 8
-            unsigned af[4];
-            ldm_x4_t(smem_u32(&sg[swz(16 * s + ga_cell, ga_ch)]), af);
-            const int kcx = xb_cell & 7, kcy = 2 * (s & 3) + (xb_cell >> 3), kcz = s >> 2;
+        const uint32_t sx = smem_u32(dsm + b * DW_BUF), sg = sx + 16u * DW_HALO;
 #pragma unroll
-            for (int o = 0; o < 4; o++) {
-                const int d = warp + 8 * o;
-                if (d < NOFF) {
-                    const int dz = d / 9 - 1, dy = (d / 3) % 3 - 1, dx = d % 3 - 1;
-                    const int h = ((kcz + dz + 1) * HT + (kcy + dy + 1)) * HT + (kcx + dx + 1);
+        for (int s = 0; s < 32; s++) {
+            unsigned af[4];
+            ldm_x4_t(sg + ga_off + 512u * s, af);
+#pragma unroll
+            for (int o = 0; o < DW_OFFS; o++) {
+                if (warp + DW_WARPS * o < NOFF) {
                     unsigned bf[4];
-                    ldm_x4_t(smem_u32(&sx[swz(h, xb_ch)]), bf);
+                    ldm_x4_t(sx + xb_off[o] + 32u * (HT * HT * (s >> 2) + HT * 2 * (s & 3)), bf);
                     // x4.trans matrices: 0 = (cells 0-7, chunk 0), 1 = (cells 8-15, chunk 0),
                     // 2 = (cells 0-7, chunk 1), 3 = (cells 8-15, chunk 1)
                     mma_bf16(acc[o][0], af, bf[0], bf[1]);
@@ -506,11 +601,12 @@ __global__ void __launch_bounds__(CONV_THREADS, 2)
                 }
             }
         }
+        __syncthreads();
     }
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int o = 0; o < 4; o++) {
-        const int d = warp + 8 * o;
+    for (int o = 0; o < DW_OFFS; o++) {
+        const int d = warp + DW_WARPS * o;
         if (d >= NOFF) continue;
 #pragma unroll
         for (int nb = 0; nb < 2; nb++) {
@@ -524,37 +620,58 @@ __global__ void __launch_bounds__(CONV_THREADS, 2)
     }
 }
 
-// G = g * (y > 0) (mask != 0) or G = g, and db[c] += sum_cells G[cell][c]
-__global__ void k_mask(const __nv_bfloat16 *gin, const __nv_bfloat16 *yact, __nv_bfloat16 *gout, float *db,
-                       int64_t ncell, int mask)
+// G = g * (y > 0) (mask != 0) or G = g, and db[c] += sum_cells G[cell][c].  16-byte accesses: chunk i of the
+// [cell][16] BF16 arrays holds channels 8 (i % 2) .. 8 (i % 2) + 7, and with an even grid stride a thread
+// keeps its chunk parity, so it sums a fixed set of 8 channels.
+__global__ void k_mask(const uint4 *gin, const uint4 *yact, uint4 *gout, float *db, int64_t ncell, int mask)
 {
     __shared__ float sdb[CONV_THREADS / 32][CH];
-    float part = 0.f;   // this thread's channel is fixed: c = threadIdx.x % 16
-    const int c = threadIdx.x & (CH - 1);
-    const int64_t total = ncell * CH;
+    float part[8] = {};
+    const int64_t total = 2 * ncell;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        float v = __bfloat162float(gin[i]);
-        if (mask && !(__bfloat162float(yact[i]) > 0.f)) v = 0.f;
-        const __nv_bfloat16 vb = __float2bfloat16_rn(v);
-        gout[i] = vb;
-        part += __bfloat162float(vb);
+        uint4 gv = gin[i];
+        unsigned *gw = reinterpret_cast<unsigned *>(&gv);
+        if (mask) {
+            const uint4 yv = yact[i];
+            const unsigned *yw = reinterpret_cast<const unsigned *>(&yv);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const bool lo = __uint_as_float(yw[k] << 16) > 0.f, hi = __uint_as_float(yw[k] & 0xffff0000u) > 0.f;
+                gw[k] &= (lo ? 0x0000ffffu : 0u) | (hi ? 0xffff0000u : 0u);
+            }
+        }
+        gout[i] = gv;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            part[2 * k] += __uint_as_float(gw[k] << 16);
+            part[2 * k + 1] += __uint_as_float(gw[k] & 0xffff0000u);
+        }
     }
-    // lanes c and c + 16 of a warp hold the same channel
-    part += __shfl_down_sync(0xffffffffu, part, 16);
-    if ((threadIdx.x & 31) < CH) sdb[threadIdx.x >> 5][c] = part;
+    // lanes of equal parity hold the same channels
+#pragma unroll
+    for (int o = 2; o < 32; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 8; k++) part[k] += __shfl_xor_sync(0xffffffffu, part[k], o);
+    const int lane = threadIdx.x & 31;
+    if (lane < 2)
+#pragma unroll
+        for (int k = 0; k < 8; k++) sdb[threadIdx.x >> 5][8 * lane + k] = part[k];
     __syncthreads();
     if (threadIdx.x < CH) {
-        float s = 0.f;
-        for (int w = 0; w < CONV_THREADS / 32; w++) s += sdb[w][threadIdx.x];
-        atomicAdd(&db[threadIdx.x], s);
+        float t = 0.f;
+        for (int w = 0; w < CONV_THREADS / 32; w++) t += sdb[w][threadIdx.x];
+        atomicAdd(&db[threadIdx.x], t);
     }
 }
 
-// loss = mean over cells and channels 0..2 of (out - tgt)^2; G = 2 (out - tgt) / (3 ncell) as BF16 [cell][16]
-__global__ void k_loss(const float *out, const float *tgt, __nv_bfloat16 *gr, double *loss, int64_t ncell)
+// loss = mean over cells and channels 0..2 of (out - tgt)^2; G = 2 (out - tgt) / (3 ncell) as BF16 [cell][16],
+// and db[c] += sum over cells of G[cell][c] (c < 3; the other channels of G are zero)
+__global__ void k_loss(const float *out, const float *tgt, __nv_bfloat16 *gr, double *loss, float *db, int64_t ncell)
 {
     __shared__ double sl[CONV_THREADS / 32];
+    __shared__ float sdb[CONV_THREADS / 32][3];
     double part = 0.0;
+    float pdb[3] = {0.f, 0.f, 0.f};
     const float sc = 2.f / (3.f * (float)ncell);
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
         __nv_bfloat162 gv[8];
@@ -568,18 +685,34 @@ __global__ void k_loss(const float *out, const float *tgt, __nv_bfloat16 *gr, do
         }
         gv[0] = __floats2bfloat162_rn(sc * d[0], sc * d[1]);
         gv[1] = __floats2bfloat162_rn(sc * d[2], 0.f);
+        pdb[0] += __low2float(gv[0]);
+        pdb[1] += __high2float(gv[0]);
+        pdb[2] += __low2float(gv[1]);
         uint4 *dst = reinterpret_cast<uint4 *>(gr + 16 * c);
         dst[0] = *reinterpret_cast<uint4 *>(&gv[0]);
         dst[1] = *reinterpret_cast<uint4 *>(&gv[4]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = part;
+    for (int o = 16; o > 0; o >>= 1) {
+        part += __shfl_down_sync(0xffffffffu, part, o);
+#pragma unroll
+        for (int a = 0; a < 3; a++) pdb[a] += __shfl_down_sync(0xffffffffu, pdb[a], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sl[threadIdx.x >> 5] = part;
+#pragma unroll
+        for (int a = 0; a < 3; a++) sdb[threadIdx.x >> 5][a] = pdb[a];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < CONV_THREADS / 32; w++) s += sl[w];
         atomicAdd(loss, s / (3.0 * (double)ncell));
+    }
+    if (threadIdx.x < 3) {
+        float t = 0.f;
+        for (int w = 0; w < CONV_THREADS / 32; w++) t += sdb[w][threadIdx.x];
+        atomicAdd(&db[threadIdx.x], t);
     }
 }
 
@@ -754,12 +887,13 @@ pm_status net_fail(pm_net *e, pm_status st, const char *msg)
 unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // the 16-channel convolution: tensor-core (tcgen05) kernel for n % 16 == 0, mma.sync kernel otherwise
-template <bool RELU, bool OUTF32>
-void launch_conv_tc(const uint4 *x, const uint4 *w, const float *b, void *y, int n, cudaStream_t st)
+template <bool RELU, bool OUTF32, bool MASK = false>
+void launch_conv_tc(const uint4 *x, const uint4 *w, const float *b, void *y, int n, cudaStream_t st,
+                    const uint4 *mact = nullptr, float *db = nullptr)
 {
     static std::atomic<uint64_t> done{0};
     if (first_on_device(done))
-        cudaFuncSetAttribute(k_conv_tc<RELU, OUTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        cudaFuncSetAttribute(k_conv_tc<RELU, OUTF32, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     const int ntiles = (n / TCX) * (n / TCY) * (n / TCZ);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -768,7 +902,7 @@ void launch_conv_tc(const uint4 *x, const uint4 *w, const float *b, void *y, int
     // PM_TEST_CONV_TIMEOUT=1 (test hook): no MMA is issued, so every bounded wait runs out
     const char *inj = std::getenv("PM_TEST_CONV_TIMEOUT");
     const int skip = inj && std::atoi(inj) != 0;
-    k_conv_tc<RELU, OUTF32><<<grid, TC_THREADS, TC_SMEM, st>>>(x, w, b, y, n, ntiles, skip);
+    k_conv_tc<RELU, OUTF32, MASK><<<grid, TC_THREADS, TC_SMEM, st>>>(x, w, b, y, n, ntiles, skip, mact, db);
 }
 
 bool conv_on_tcgen05(int n) { return n % TCY == 0; }
@@ -815,6 +949,13 @@ int dw_blocks(int n)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int ntiles = (n / TT) * (n / TT) * (n / TT);
     return std::max(1, std::min(ntiles, 2 * std::max(sms, 1)));
+}
+
+void launch_conv_dw(const uint4 *x, const uint4 *g, float *dw, int n, cudaStream_t st)
+{
+    static std::atomic<uint64_t> done{0};
+    if (first_on_device(done)) cudaFuncSetAttribute(k_conv_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DW_SMEM);
+    k_conv_dw<<<dw_blocks(n), 32 * DW_WARPS, DW_SMEM, st>>>(x, g, dw, n);
 }
 
 bool valid_net_n(int n) { return n >= 8 && n <= 1024 && n % 8 == 0; }
@@ -951,18 +1092,33 @@ pm_status pm_net_backward(pm_net *e, const float *target, double *loss)
     const int n = e->n;
     net_forward(e);
     cudaMemsetAsync(e->dloss, 0, sizeof(double), e->stream);
-    k_loss<<<std::min<int64_t>(grid_for(nc, CONV_THREADS), 4096), CONV_THREADS, 0, e->stream>>>(e->out, target, e->g0,
-                                                                                                  e->dloss, nc);
-    const unsigned mblocks = (unsigned)std::min<int64_t>(grid_for(nc * CH, CONV_THREADS), 4096);
-    const int dwb = dw_blocks(n);
+    // G = dL/d(network output) and the bias gradient of the last layer (no activation)
+    k_loss<<<std::min<int64_t>(grid_for(nc, CONV_THREADS), 4096), CONV_THREADS, 0, e->stream>>>(
+        e->out, target, e->g0, e->dloss, e->grad + (size_t)(NL - 1) * PSZ + WSZ, nc);
+    const unsigned mblocks = (unsigned)std::min<int64_t>(grid_for(2 * nc, CONV_THREADS), 4096);
+    // tensor-core meshes: the input-gradient convolution of layer l applies the ReLU derivative of layer
+    // l - 1 and sums that layer's bias gradient in its epilogue; other meshes run k_mask after it
+    const bool fused = conv_on_tcgen05(n);
     __nv_bfloat16 *g = e->g0, *h = e->g1;
     for (int l = NL - 1; l >= 0; l--) {
-        // g holds dL/d(output of layer l); mask by the ReLU and accumulate the bias gradient
-        k_mask<<<mblocks, CONV_THREADS, 0, e->stream>>>(g, l < NL - 1 ? e->act[l + 1] : g, h,
-                                                        e->grad + (size_t)l * PSZ + WSZ, nc, l < NL - 1);
-        k_conv_dw<<<dwb, CONV_THREADS, 0, e->stream>>>(reinterpret_cast<const uint4 *>(e->act[l]),
-                                                      reinterpret_cast<const uint4 *>(h), e->grad + (size_t)l * PSZ, n);
-        if (l > 0) conv_launch(e, l, h, g, true, false, false);   // dL/d(output of layer l - 1)
+        // g holds dL/d(pre-activation of layer l), or, unfused and l < NL - 1, dL/d(output of layer l)
+        if (!fused && l < NL - 1) {
+            k_mask<<<mblocks, CONV_THREADS, 0, e->stream>>>(
+                reinterpret_cast<const uint4 *>(g), reinterpret_cast<const uint4 *>(e->act[l + 1]),
+                reinterpret_cast<uint4 *>(h), e->grad + (size_t)l * PSZ + WSZ, nc, 1);
+            std::swap(g, h);
+        }
+        launch_conv_dw(reinterpret_cast<const uint4 *>(e->act[l]), reinterpret_cast<const uint4 *>(g),
+                       e->grad + (size_t)l * PSZ, n, e->stream);
+        if (l == 0) break;
+        const uint4 *wt = reinterpret_cast<const uint4 *>(e->wt + (size_t)l * WSZ);
+        if (fused)
+            launch_conv_tc<false, false, true>(reinterpret_cast<const uint4 *>(g), wt, nullptr, h, n, e->stream,
+                                               reinterpret_cast<const uint4 *>(e->act[l]),
+                                               e->grad + (size_t)(l - 1) * PSZ + WSZ);
+        else
+            conv_launch(e, l, g, h, true, false, false);   // dL/d(output of layer l - 1)
+        std::swap(g, h);
     }
     cudaError_t ce = cudaGetLastError();
     if (ce == cudaSuccess && loss) {
@@ -1110,8 +1266,8 @@ pm_status pm_conv3d_backward_weight(int32_t n, const void *x, const void *g, flo
 {
     if (!valid_net_n(n)) return PM_ERR_UNSUPPORTED_SIZE;
     if (!x || !g || !dw) return PM_ERR_INVALID_ARG;
-    k_conv_dw<<<dw_blocks(n), CONV_THREADS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        static_cast<const uint4 *>(x), static_cast<const uint4 *>(g), dw, n);
+    launch_conv_dw(static_cast<const uint4 *>(x), static_cast<const uint4 *>(g), dw, n,
+                   reinterpret_cast<cudaStream_t>(stream));
     return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
 }
 

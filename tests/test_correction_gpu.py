@@ -154,9 +154,11 @@ def _net_with_inputs(torch, pm, n, seed):
     return net, flat_r, uncl(xr, 2, n)
 
 
-def test_network_loss_and_gradients_match_oracle(env):
+@pytest.mark.parametrize("n", [16, 24])
+def test_network_loss_and_gradients_match_oracle(env, n):
+    """16^3 runs the tensor-core path, whose input-gradient convolutions apply the ReLU derivative and sum the
+    bias gradients in their epilogue; 24^3 runs the mma.sync convolutions and the separate mask kernel."""
     torch, pm = env
-    n = 16
     net, flat, x = _net_with_inputs(torch, pm, n, 5)
     rng = np.random.default_rng(6)
     tgt = np.zeros((n ** 3, 8), dtype=np.float32)

@@ -432,8 +432,11 @@ def schedule_phases(pm, torch, n, n_part, box, d_pos, d_mom, stream, block=10):
         ev1.record(stream)
         torch.cuda.synchronize()
         per_kernel, _ = pm.pm_get_timings(sim.ctx)
+        ms = ev0.elapsed_time(ev1) / k
         out.append({"steps": f"{b0}-{b0 + k - 1}", "z": [round(1 / a_n[b0] - 1, 2), round(1 / a_n[b0 + k - 1] - 1, 3)],
-                    "ms_per_step": round(ev0.elapsed_time(ev1) / k, 3),
+                    "ms_per_step": round(ms, 3),
+                    "step_roofline_frac": round(method_bytes_per_update(True) * n_part / (ms * 1e-3) / 1e9 /
+                                                load_peaks()[0], 4),
                     "kernels_ms": {key: round(per_kernel[key], 3) for key in
                                    ("project", "fft_fwd", "solve", "fft_inv", "kick_drift", "sort")}})
     sim.close()
@@ -757,6 +760,19 @@ def main():
     ms_max = max_ranks(ms_mixed)
     value = whole_job_rate(world, n_part, ms_max)
 
+    # the next steps of the same run as graph-replayed pm_step calls (one captured graph per step)
+    sim.step_graph(True)
+    sim.step()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = max_ranks(ev0.elapsed_time(ev1) / args.steps)
+    sim.step_graph(False)
+
     # end to end through the C ABI with pinned host buffers: upload the state, step, read it back
     h_pos = torch.from_numpy(pos).pin_memory()
     h_mom = torch.from_numpy(mom).pin_memory()
@@ -885,7 +901,8 @@ def main():
         line = {
             "metric": METRIC,
             "value": value, "unit": "particle-updates/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_max, "graph_ms_per_step": round(graph_ms, 4),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(n, box, args.warmup, args.steps, world), ic_seconds=round(t_ic, 1)),
             "kernels_ms": {k: round(v, 4) for k, v in kern.items()},

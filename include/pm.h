@@ -158,8 +158,20 @@ pm_status pm_solve(pm_ctx *ctx);
  * Advances the step index.  Errors: STATE (pm_solve not called), CUDA. */
 pm_status pm_update(pm_ctx *ctx);
 
-/* pm_project + pm_solve + pm_update. */
+/* pm_project + pm_solve + pm_update.  With pm_step_graph(ctx, 1) the step's
+ * launches are captured into one CUDA graph on a stream of the context and
+ * the graph is launched on the context's stream (the executable graph of the
+ * previous step is updated in place); called while the caller captures the
+ * context's stream, the step is issued as plain launches into that capture.
+ * Errors: as the three calls, CUDA (capture, instantiation, launch). */
 pm_status pm_step(pm_ctx *ctx);
+
+/* Graph-captured pm_step on (1) or off (0, the default).  Graph steps run
+ * the same kernels in the same order as plain steps (the results differ only
+ * through the order of particles inside a cell, which the counting sort
+ * leaves open) and record no per-kernel timings (pm_get_timings reports the
+ * plain steps only).  Errors: INVALID_ARG. */
+pm_status pm_step_graph(pm_ctx *ctx, int32_t on);
 
 /* Replace the particle state between steps without touching the fields,
  * the step index or the tensor state: pos, mom [n_part][3] f64 (host or

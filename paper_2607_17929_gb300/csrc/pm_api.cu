@@ -778,6 +778,8 @@ void pm_destroy(pm_ctx *ctx)
     for (auto &row : c.evr)
         for (auto &e : row)
             if (e) cudaEventDestroy(e);
+    if (c.gexec) cudaGraphExecDestroy(c.gexec);
+    if (c.gstream) cudaStreamDestroy(c.gstream);
     cudaGetLastError();
     delete ctx;
 }
@@ -889,13 +891,82 @@ pm_status pm_update(pm_ctx *ctx)
     return PM_OK;
 }
 
-pm_status pm_step(pm_ctx *ctx)
+static pm_status step_plain(pm_ctx *ctx)
 {
     pm_status st = pm_project(ctx);
     if (st) return st;
     st = pm_solve(ctx);
     if (st) return st;
     return pm_update(ctx);
+}
+
+// one step captured into a graph on the context's capture stream, then launched on its stream; the
+// executable graph of the previous step is updated in place when the topology is unchanged
+static pm_status step_graph(pm_ctx *ctx)
+{
+    Ctx &c = ctx->c;
+    if (!c.gstream && cudaStreamCreateWithFlags(&c.gstream, cudaStreamNonBlocking) != cudaSuccess) {
+        c.gstream = nullptr;
+        return cuda_fail(c, cudaGetLastError(), "pm_step: capture stream");
+    }
+    cudaStream_t user = c.stream;
+    cudaError_t ce = cudaStreamBeginCapture(c.gstream, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "pm_step: cudaStreamBeginCapture");
+    c.stream = c.gstream;
+    c.no_timing = true;
+    const pm_status st = step_plain(ctx);
+    c.no_timing = false;
+    c.stream = user;
+    cudaGraph_t graph = nullptr;
+    ce = cudaStreamEndCapture(c.gstream, &graph);
+    if (st != PM_OK) {
+        // the host state of a failed call is unchanged or the context is poisoned; nothing was launched
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st;
+    }
+    if (ce != cudaSuccess || !graph) return cuda_fail(c, ce != cudaSuccess ? ce : cudaErrorUnknown, "pm_step: capture");
+    bool updated = false;
+    if (c.gexec) {
+        cudaGraphExecUpdateResultInfo info{};
+        updated = cudaGraphExecUpdate(c.gexec, graph, &info) == cudaSuccess;
+        if (!updated) cudaGetLastError();
+    }
+    if (!updated) {
+        if (c.gexec) cudaGraphExecDestroy(c.gexec);
+        c.gexec = nullptr;
+        ce = cudaGraphInstantiate(&c.gexec, graph, 0);
+        if (ce != cudaSuccess) {
+            c.gexec = nullptr;
+            cudaGraphDestroy(graph);
+            return cuda_fail(c, ce, "pm_step: cudaGraphInstantiate");
+        }
+    }
+    cudaGraphDestroy(graph);
+    ce = cudaGraphLaunch(c.gexec, c.stream);
+    return ce == cudaSuccess ? PM_OK : cuda_fail(c, ce, "pm_step: cudaGraphLaunch");
+}
+
+pm_status pm_step(pm_ctx *ctx)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    // inside a capture by the caller (the ensemble) the step is issued as plain launches
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (ctx->c.graph_step && cudaStreamIsCapturing(ctx->c.stream, &cs) == cudaSuccess &&
+        cs == cudaStreamCaptureStatusNone)
+        return step_graph(ctx);
+    cudaGetLastError();
+    return step_plain(ctx);
+}
+
+pm_status pm_step_graph(pm_ctx *ctx, int32_t on)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    if (on != 0 && on != 1) return fail(ctx->c, PM_ERR_INVALID_ARG, "pm_step_graph: on must be 0 or 1");
+    ctx->c.graph_step = on != 0;
+    return PM_OK;
 }
 
 pm_status pm_get_particles(pm_ctx *ctx, double *pos, double *mom)

@@ -137,7 +137,12 @@ struct Ctx {
     int64_t window = 0;       // completed steps in the current timing window
     int64_t launches = 0, launches_mark = 0;
 
-    bool no_timing = false;   // set while a step is captured into a CUDA graph (ensemble)
+    bool no_timing = false;   // set while a step is captured into a CUDA graph (ensemble, pm_step_graph)
+
+    // pm_step_graph: each pm_step is captured on gstream into one graph, kept in gexec and launched on stream
+    bool graph_step = false;
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
 
     void mark(int point)
     {

@@ -55,6 +55,7 @@ def _load():
         "pm_solve": ([vp], C.c_int),
         "pm_update": ([vp], C.c_int),
         "pm_step": ([vp], C.c_int),
+        "pm_step_graph": ([vp, C.c_int32], C.c_int),
         "pm_get_particles": ([vp, vp, vp], C.c_int),
         "pm_get_field": ([vp, C.c_int, vp], C.c_int),
         "pm_get_tensor": ([vp, C.c_int, vp], C.c_int),
@@ -113,7 +114,7 @@ def _load():
 lib = _load()
 
 EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_project", "pm_solve",
-            "pm_update", "pm_step", "pm_put_particles", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
+            "pm_update", "pm_step", "pm_step_graph", "pm_put_particles", "pm_get_particles", "pm_get_field", "pm_get_tensor", "pm_power_spectrum",
             "pm_power_spectrum_noalloc", "pm_ensemble_init", "pm_ensemble_destroy", "pm_ensemble_last_error",
             "pm_ensemble_box", "pm_ensemble_set_particles", "pm_ensemble_step", "pm_ensemble_sync", "pm_ensemble_tune",
             "pm_ensemble_stream", "pm_ensemble_set_streams", "pm_net_param_count", "pm_net_create", "pm_net_destroy", "pm_net_last_error",
@@ -191,6 +192,11 @@ def pm_update(ctx):
 
 def pm_step(ctx):
     _check(ctx, lib.pm_step(ctx))
+
+
+def pm_step_graph(ctx, on):
+    """pm_step as one captured CUDA graph per step (on=1) or as plain launches (on=0, the default)."""
+    _check(ctx, lib.pm_step_graph(ctx, int(on)))
 
 
 def pm_put_particles(ctx, pos, mom):
@@ -529,6 +535,9 @@ class PM:
 
     def step(self):
         pm_step(self.ctx)
+
+    def step_graph(self, on=True):
+        pm_step_graph(self.ctx, 1 if on else 0)
 
     def project(self):
         pm_project(self.ctx)

@@ -809,6 +809,22 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_packed_ms = max_ranks(1e3 * (time.perf_counter() - t0) / args.e2e_steps)
+    # the same loop through the overlapped calls: each step's upload and the previous step's download run
+    # on copy engines beside the steps (pinned host records; every step still moves its inputs in and its
+    # result out)
+    pm.pm_put_particles_packed_async(sim.ctx, n_part, h_rec)
+    sim.step()
+    pm.pm_get_particles_packed_async(sim.ctx, n_part, o_rec)
+    pm.pm_io_wait(sim.ctx)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        pm.pm_put_particles_packed_async(sim.ctx, n_part, h_rec)
+        sim.step()
+        pm.pm_get_particles_packed_async(sim.ctx, n_part, o_rec)
+    pm.pm_io_wait(sim.ctx)
+    barrier()
+    e2e_async_ms = max_ranks(1e3 * (time.perf_counter() - t0) / args.e2e_steps)
     del h_rec, o_rec
     sim.close()
     del sim
@@ -918,11 +934,17 @@ def main():
             "cufft_comparison": cufft,
             "schedule_phases": phases,
             "config2_fp64_vs_mixed": config2,
-            "e2e": {"value": world * n_part / (e2e_packed_ms * 1e-3), "unit": "particle-updates/s",
-                    "ms_per_step": e2e_packed_ms, "h2d_bytes_per_step": 28 * n_part, "d2h_bytes_per_step": 28 * n_part,
-                    "how": "every step: pm_put_particles_packed from pinned host records (int32 cell, 3 f32 offsets, "
-                           "3 f32 momenta: the state the mixed step holds) + pm_step + pm_get_particles_packed into "
-                           "pinned host memory"},
+            "e2e": {"value": world * n_part / (e2e_async_ms * 1e-3), "unit": "particle-updates/s",
+                    "ms_per_step": e2e_async_ms, "h2d_bytes_per_step": 28 * n_part, "d2h_bytes_per_step": 28 * n_part,
+                    "how": "every step: pm_put_particles_packed_async from pinned host records (int32 cell, 3 f32 "
+                           "offsets, 3 f32 momenta: the state the mixed step holds) + pm_step + "
+                           "pm_get_particles_packed_async into pinned host memory; the copies run on copy engines "
+                           "beside the steps; pm_io_wait closes the timed region"},
+            "e2e_sync": {"value": world * n_part / (e2e_packed_ms * 1e-3), "unit": "particle-updates/s",
+                         "ms_per_step": e2e_packed_ms, "h2d_bytes_per_step": 28 * n_part,
+                         "d2h_bytes_per_step": 28 * n_part,
+                         "how": "the same loop through the synchronous pm_put_particles_packed / "
+                                "pm_get_particles_packed"},
             "e2e_f64": {"value": world * n_part / (e2e_ms * 1e-3), "unit": "particle-updates/s", "ms_per_step": e2e_ms,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                         "how": "every step: pm_put_particles(pinned host f64 pos, mom) + pm_step + "

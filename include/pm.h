@@ -209,6 +209,31 @@ pm_status pm_set_particles_packed(pm_ctx *ctx, const pm_packed_particle *p);
 pm_status pm_put_particles_packed(pm_ctx *ctx, const pm_packed_particle *p);
 pm_status pm_get_particles_packed(pm_ctx *ctx, pm_packed_particle *p);
 
+/* Overlapped forms of pm_put_particles_packed / pm_get_particles_packed for a
+ * loop that feeds every step from the host and reads every result back:
+ * both return at once.  The records travel by copy engine on two streams of
+ * the context, so an upload and a download run beside the steps on the
+ * context's stream and beside each other.  put: the n_part records of p go to
+ * a device staging buffer (after the previous put's records left it), and in
+ * stream order with the steps they are checked, become the particle state
+ * and are sorted by cell.  get: in stream order, the state in id order goes
+ * to a second staging buffer (after the previous get's download left it),
+ * then downloads into p.  p should be pinned host memory (pageable memory
+ * makes the copies synchronous); a put's p must stay unchanged and a get's p
+ * unread until pm_io_wait returns.  A bad record (as for
+ * pm_put_particles_packed) is neutralised on the device and reported by
+ * pm_io_wait, after which the context has no particles.  Staging takes 2 x 28
+ * bytes a particle, allocated on first use.  Mixed contexts only.  Errors:
+ * INVALID_ARG (NULL, FP64 context), STATE (no particles yet or mid-step), OOM,
+ * CUDA. */
+pm_status pm_put_particles_packed_async(pm_ctx *ctx, const pm_packed_particle *p);
+pm_status pm_get_particles_packed_async(pm_ctx *ctx, pm_packed_particle *p);
+
+/* Wait for the context's stream and both I/O streams; report a bad record of
+ * a put since the previous wait (INVALID_ARG; the context then has no
+ * particles).  Errors: INVALID_ARG, CUDA. */
+pm_status pm_io_wait(pm_ctx *ctx);
+
 /* One N^3 real field as f64 (see PM_FIELD_*), [z][y][x].  Errors: INVALID_ARG, STATE, CUDA. */
 pm_status pm_get_field(pm_ctx *ctx, int field_id, double *dst);
 

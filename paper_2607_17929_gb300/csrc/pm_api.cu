@@ -617,6 +617,38 @@ static pm_status guard(pm_ctx *ctx)
     return PM_OK;
 }
 
+// streams, events and staging buffers of the overlapped packed I/O, made on first use
+static pm_status io_setup(Ctx &c)
+{
+    if (c.io_up) return PM_OK;
+    const size_t bytes = sizeof(pm_packed_particle) * (size_t)c.np;
+    bool ok = cudaMalloc(&c.in_stage, bytes) == cudaSuccess && cudaMalloc(&c.out_stage, bytes) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (c.in_stage) cudaFree(c.in_stage);
+        c.in_stage = c.out_stage = nullptr;
+        return fail(c, PM_ERR_OOM, "particle I/O staging buffers");
+    }
+    ok = cudaStreamCreateWithFlags(&c.io_up, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&c.io_down, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t *e : {&c.ev_in_ready, &c.ev_in_free, &c.ev_out_ready, &c.ev_out_free})
+        ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cuda_fail(c, cudaGetLastError(), "particle I/O streams");
+    return PM_OK;
+}
+
+static void io_release(Ctx &c)
+{
+    if (c.io_up) cudaStreamSynchronize(c.io_up);
+    if (c.io_down) cudaStreamSynchronize(c.io_down);
+    for (cudaEvent_t e : {c.ev_in_ready, c.ev_in_free, c.ev_out_ready, c.ev_out_free})
+        if (e) cudaEventDestroy(e);
+    if (c.io_up) cudaStreamDestroy(c.io_up);
+    if (c.io_down) cudaStreamDestroy(c.io_down);
+    if (c.in_stage) cudaFree(c.in_stage);
+    if (c.out_stage) cudaFree(c.out_stage);
+}
+
 extern "C" {
 
 pm_status pm_init(const pm_config *cfg, pm_ctx **out)
@@ -780,6 +812,7 @@ void pm_destroy(pm_ctx *ctx)
             if (e) cudaEventDestroy(e);
     if (c.gexec) cudaGraphExecDestroy(c.gexec);
     if (c.gstream) cudaStreamDestroy(c.gstream);
+    io_release(c);
     cudaGetLastError();
     delete ctx;
 }
@@ -838,6 +871,75 @@ pm_status pm_get_particles_packed(pm_ctx *ctx, pm_packed_particle *p)
     if (!c.mixed) return fail(c, PM_ERR_INVALID_ARG, "pm_get_particles_packed: packed records need a mixed context");
     if (!c.have_particles) return fail(c, PM_ERR_STATE, "pm_get_particles_packed: no particles");
     return get_packed_t(c, p);
+}
+
+pm_status pm_put_particles_packed_async(pm_ctx *ctx, const pm_packed_particle *p)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (!p) return fail(c, PM_ERR_INVALID_ARG, "pm_put_particles_packed_async: NULL array");
+    if (!c.mixed) return fail(c, PM_ERR_INVALID_ARG, "pm_put_particles_packed_async: packed records need a mixed context");
+    if (!c.have_particles || c.stage != 0) return fail(c, PM_ERR_STATE, "pm_put_particles_packed_async: not between steps");
+    if ((g = io_setup(c))) return g;
+    const size_t bytes = sizeof(pm_packed_particle) * (size_t)c.np;
+    // upload (copy engine) once the previous put's records have been read out of the staging buffer
+    CK(cudaStreamWaitEvent(c.io_up, c.ev_in_free, 0));
+    CK(cudaMemcpyAsync(c.in_stage, p, bytes, cudaMemcpyDefault, c.io_up));
+    CK(cudaEventRecord(c.ev_in_ready, c.io_up));
+    // then, in stream order with the steps: check and load the records, free the staging buffer, sort
+    CK(cudaStreamWaitEvent(c.stream, c.ev_in_ready, 0));
+    CK(cudaMemsetAsync(c.count, 0, sizeof(int32_t) * c.nc, c.stream));
+    launch_load_packed(c, reinterpret_cast<const pm_packed_particle *>(c.in_stage), 0, c.np,
+                       reinterpret_cast<int *>(c.dscal + 5));
+    CKL("load_packed");
+    CK(cudaEventRecord(c.ev_in_free, c.stream));
+    launch_sort<float>(c);
+    CKL("sort");
+    return PM_OK;
+}
+
+pm_status pm_get_particles_packed_async(pm_ctx *ctx, pm_packed_particle *p)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (!p) return fail(c, PM_ERR_INVALID_ARG, "pm_get_particles_packed_async: NULL array");
+    if (!c.mixed) return fail(c, PM_ERR_INVALID_ARG, "pm_get_particles_packed_async: packed records need a mixed context");
+    if (!c.have_particles || c.stage != 0) return fail(c, PM_ERR_STATE, "pm_get_particles_packed_async: not between steps");
+    if ((g = io_setup(c))) return g;
+    const size_t bytes = sizeof(pm_packed_particle) * (size_t)c.np;
+    // in stream order: the state in id order into the output staging buffer, once the previous get's
+    // download has read it out
+    CK(cudaStreamWaitEvent(c.stream, c.ev_out_free, 0));
+    launch_store_particles_scatter<float>(c, nullptr, nullptr);
+    CKL("unpermute");
+    launch_store_packed(c, reinterpret_cast<pm_packed_particle *>(c.out_stage), 0, c.np);
+    CKL("store_packed");
+    CK(cudaEventRecord(c.ev_out_ready, c.stream));
+    // download (copy engine) beside the following steps
+    CK(cudaStreamWaitEvent(c.io_down, c.ev_out_ready, 0));
+    CK(cudaMemcpyAsync(p, c.out_stage, bytes, cudaMemcpyDefault, c.io_down));
+    CK(cudaEventRecord(c.ev_out_free, c.io_down));
+    return PM_OK;
+}
+
+pm_status pm_io_wait(pm_ctx *ctx)
+{
+    pm_status g = guard(ctx);
+    if (g) return g;
+    Ctx &c = ctx->c;
+    if (c.io_up) CK(cudaStreamSynchronize(c.io_up));
+    if (c.io_down) CK(cudaStreamSynchronize(c.io_down));
+    CK(cudaStreamSynchronize(c.stream));
+    int bad = 0;
+    int *flag = reinterpret_cast<int *>(c.dscal + 5);
+    CK(cudaMemcpy(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!bad) return PM_OK;
+    CK(cudaMemset(flag, 0, sizeof(int)));
+    c.have_particles = false;
+    return fail(c, PM_ERR_INVALID_ARG, "pm_io_wait: a record put since the last wait had a cell out of range, an offset "
+                                       "outside [0, 1) or a non-finite value; the particle state is invalid");
 }
 
 pm_status pm_project(pm_ctx *ctx)

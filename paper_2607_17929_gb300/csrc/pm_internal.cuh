@@ -123,7 +123,8 @@ struct Ctx {
     void *ktab = nullptr;       // N values of ktilde(n)
     void *tw = nullptr;         // N twiddles exp(-2 pi i k / N)
     void *tw2 = nullptr;        // per-stage twiddles of the compile-time-N passes
-    double *dscal = nullptr;    // device f64 scalars: [0] k=0 particle sum, [1] mean phi_{n-1}, [2] mean phi_n
+    double *dscal = nullptr;    // device f64 scalars: [0] k=0 particle sum, [1..3] mean phi per ring slot,
+                                // [4] (int) record check of a load, [5] (int) latched check of the async puts
     void *stage_buf = nullptr;  // host-transfer staging (f64)
     int64_t stage_elems = 0;
     FftPlan plan;
@@ -143,6 +144,12 @@ struct Ctx {
     bool graph_step = false;
     cudaStream_t gstream = nullptr;
     cudaGraphExec_t gexec = nullptr;
+
+    // overlapped packed I/O (pm_put_particles_packed_async / pm_get_particles_packed_async): copy-engine
+    // transfers on their own streams between pinned host memory and two device staging buffers
+    cudaStream_t io_up = nullptr, io_down = nullptr;
+    cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
+    void *in_stage = nullptr, *out_stage = nullptr;   // n_part packed records each
 
     void mark(int point)
     {

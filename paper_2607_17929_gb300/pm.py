@@ -68,6 +68,9 @@ def _load():
         "pm_set_particles_packed": ([vp, vp], C.c_int),
         "pm_put_particles_packed": ([vp, vp], C.c_int),
         "pm_get_particles_packed": ([vp, vp], C.c_int),
+        "pm_put_particles_packed_async": ([vp, vp], C.c_int),
+        "pm_get_particles_packed_async": ([vp, vp], C.c_int),
+        "pm_io_wait": ([vp], C.c_int),
         "pm_ensemble_set_batched": ([vp, i32], C.c_int),
         "pm_ensemble_get_mode": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "pm_put_particles": ([vp, vp, vp], C.c_int),
@@ -123,7 +126,8 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_last_error", "pm_set_particles", "pm_pr
             "pm_set_correction", "pm_net_set_scales", "pm_conv3d_forward", "pm_conv3d_backward_weight", "pm_conv3d_check",
             "pm_get_time", "pm_get_schedule", "pm_get_timings", "pm_fft_shapes", "pm_deposit_shape", "pm_save",
             "pm_load", "pm_ensemble_set_batched", "pm_ensemble_get_mode", "pm_set_particles_packed",
-            "pm_put_particles_packed", "pm_get_particles_packed"]
+            "pm_put_particles_packed", "pm_get_particles_packed", "pm_put_particles_packed_async",
+            "pm_get_particles_packed_async", "pm_io_wait"]
 
 
 def _ptr(a):
@@ -303,6 +307,20 @@ def pm_put_particles_packed(ctx, n_part, records):
 
 def pm_get_particles_packed(ctx, n_part, records):
     _check(ctx, lib.pm_get_particles_packed(ctx, _packed_ptr(records, n_part)))
+
+
+def pm_put_particles_packed_async(ctx, n_part, records):
+    """Overlapped put: returns at once; `records` (pinned) must stay unchanged until pm_io_wait."""
+    _check(ctx, lib.pm_put_particles_packed_async(ctx, _packed_ptr(records, n_part)))
+
+
+def pm_get_particles_packed_async(ctx, n_part, records):
+    """Overlapped get: returns at once; `records` (pinned) holds the state once pm_io_wait returns."""
+    _check(ctx, lib.pm_get_particles_packed_async(ctx, _packed_ptr(records, n_part)))
+
+
+def pm_io_wait(ctx):
+    _check(ctx, lib.pm_io_wait(ctx))
 
 
 def pm_deposit_shape(ctx, force=-1):

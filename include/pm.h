@@ -160,8 +160,8 @@ pm_status pm_update(pm_ctx *ctx);
 
 /* pm_project + pm_solve + pm_update.  With pm_step_graph(ctx, 1) the step's
  * launches are captured into one CUDA graph on a stream of the context and
- * the graph is launched on the context's stream (the executable graph of the
- * previous step is updated in place); called while the caller captures the
+ * the graph is launched on the context's stream (two executable graphs
+ * alternate and are updated in place); called while the caller captures the
  * context's stream, the step is issued as plain launches into that capture.
  * Errors: as the three calls, CUDA (capture, instantiation, launch). */
 pm_status pm_step(pm_ctx *ctx);

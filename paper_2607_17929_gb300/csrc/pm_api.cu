@@ -810,7 +810,8 @@ void pm_destroy(pm_ctx *ctx)
     for (auto &row : c.evr)
         for (auto &e : row)
             if (e) cudaEventDestroy(e);
-    if (c.gexec) cudaGraphExecDestroy(c.gexec);
+    for (cudaGraphExec_t x : c.gexec)
+        if (x) cudaGraphExecDestroy(x);
     if (c.gstream) cudaStreamDestroy(c.gstream);
     io_release(c);
     cudaGetLastError();
@@ -1003,7 +1004,8 @@ static pm_status step_plain(pm_ctx *ctx)
 }
 
 // one step captured into a graph on the context's capture stream, then launched on its stream; the
-// executable graph of the previous step is updated in place when the topology is unchanged
+// executable graph of the step before the previous one is updated in place when the topology is unchanged
+// (two alternate, so an update never waits for the graph that is still running)
 static pm_status step_graph(pm_ctx *ctx)
 {
     Ctx &c = ctx->c;
@@ -1028,24 +1030,26 @@ static pm_status step_graph(pm_ctx *ctx)
         return st;
     }
     if (ce != cudaSuccess || !graph) return cuda_fail(c, ce != cudaSuccess ? ce : cudaErrorUnknown, "pm_step: capture");
+    cudaGraphExec_t &x = c.gexec[c.gslot];
+    c.gslot ^= 1;
     bool updated = false;
-    if (c.gexec) {
+    if (x) {
         cudaGraphExecUpdateResultInfo info{};
-        updated = cudaGraphExecUpdate(c.gexec, graph, &info) == cudaSuccess;
+        updated = cudaGraphExecUpdate(x, graph, &info) == cudaSuccess;
         if (!updated) cudaGetLastError();
     }
     if (!updated) {
-        if (c.gexec) cudaGraphExecDestroy(c.gexec);
-        c.gexec = nullptr;
-        ce = cudaGraphInstantiate(&c.gexec, graph, 0);
+        if (x) cudaGraphExecDestroy(x);
+        x = nullptr;
+        ce = cudaGraphInstantiate(&x, graph, 0);
         if (ce != cudaSuccess) {
-            c.gexec = nullptr;
+            x = nullptr;
             cudaGraphDestroy(graph);
             return cuda_fail(c, ce, "pm_step: cudaGraphInstantiate");
         }
     }
     cudaGraphDestroy(graph);
-    ce = cudaGraphLaunch(c.gexec, c.stream);
+    ce = cudaGraphLaunch(x, c.stream);
     return ce == cudaSuccess ? PM_OK : cuda_fail(c, ce, "pm_step: cudaGraphLaunch");
 }
 

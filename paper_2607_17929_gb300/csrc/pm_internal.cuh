@@ -140,10 +140,12 @@ struct Ctx {
 
     bool no_timing = false;   // set while a step is captured into a CUDA graph (ensemble, pm_step_graph)
 
-    // pm_step_graph: each pm_step is captured on gstream into one graph, kept in gexec and launched on stream
+    // pm_step_graph: each pm_step is captured on gstream into one graph and launched on stream; two
+    // executable graphs alternate, so the one being updated is never the one still running
     bool graph_step = false;
     cudaStream_t gstream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gslot = 0;
 
     // overlapped packed I/O (pm_put_particles_packed_async / pm_get_particles_packed_async): copy-engine
     // transfers on their own streams between pinned host memory and two device staging buffers

@@ -688,6 +688,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-correction", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="correction leg without its training run and gain")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-phases", action="store_true")
     ap.add_argument("--no-config2", action="store_true")
@@ -760,18 +761,6 @@ def main():
     ms_max = max_ranks(ms_mixed)
     value = whole_job_rate(world, n_part, ms_max)
 
-    # the next steps of the same run as graph-replayed pm_step calls (one captured graph per step)
-    sim.step_graph(True)
-    sim.step()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        sim.step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    graph_ms = max_ranks(ev0.elapsed_time(ev1) / args.steps)
-    sim.step_graph(False)
 
     # end to end through the C ABI with pinned host buffers: upload the state, step, read it back
     h_pos = torch.from_numpy(pos).pin_memory()
@@ -829,6 +818,26 @@ def main():
     sim.close()
     del sim
 
+    # the same steps of the schedule as graph-replayed pm_step calls (one captured graph per step)
+    gsim = pm.PM(n, n_part, box, OM, ZI, 0.0, N_STEPS_SCHEDULE, pm.PM_MIXED, 0, stream)
+    gsim.set_particles(d_pos, d_mom)
+    for _ in range(args.warmup - 1):
+        gsim.step()
+    gsim.step_graph(True)
+    gsim.step()   # instantiates the executable graphs
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        gsim.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    graph_ms = max_ranks(ev0.elapsed_time(ev1) / args.steps)
+    gsim.close()
+    del gsim
+
     # the whole schedule in blocks of 10 steps (early vs late, clustered steps)
     phases = None
     if not args.no_phases:
@@ -871,7 +880,7 @@ def main():
 
     correction = None
     if not args.no_correction:
-        correction = correction_bench(pm, torch)
+        correction = correction_bench(pm, torch, train=not args.no_train)
         torch.cuda.empty_cache()
 
     cufft = None

@@ -49,9 +49,11 @@ def uncl(y, c, n):
     return np.ascontiguousarray(y[:, :c].T).reshape(c, n, n, n)
 
 
-@pytest.mark.parametrize("n,relu", [(8, True), (16, False), (24, True), (32, True), (48, False)])
+@pytest.mark.parametrize("n,relu", [(8, True), (16, False), (24, True), (32, True), (48, False), (64, True)])
 def test_conv_forward_bf16_matches_oracle(env, n, relu):
-    """Meshes with n % 16 == 0 run the tcgen05 kernel (8 x 16 x 4 cell tiles), the others the mma.sync one."""
+    """Meshes with n % 16 == 0 run the tcgen05 kernel (8 x 16 x 4 cell tiles), the others the mma.sync one.  At
+    64^3 (512 tiles for at most 304 persistent CTAs) a CTA reads one tile's accumulator back while the tensor
+    core works on the next."""
     torch, pm = env
     rng = np.random.default_rng(n)
     x_t, x = bf16(torch, cl(rng.standard_normal((16, n, n, n))))
@@ -156,10 +158,11 @@ def _net_with_inputs(torch, pm, n, seed):
     return net, flat_r, uncl(xr, 2, n)
 
 
-@pytest.mark.parametrize("n", [16, 24])
+@pytest.mark.parametrize("n", [16, 24, 64])
 def test_network_loss_and_gradients_match_oracle(env, n):
-    """16^3 runs the tensor-core path, whose input-gradient convolutions apply the ReLU derivative and sum the
-    bias gradients in their epilogue; 24^3 runs the mma.sync convolutions and the separate mask kernel."""
+    """16^3 and 64^3 run the tensor-core path, whose input-gradient convolutions apply the ReLU derivative and sum
+    the bias gradients in their epilogue (at 64^3 over several tiles per persistent CTA); 24^3 runs the mma.sync
+    convolutions and the separate mask kernel."""
     torch, pm = env
     net, flat, x = _net_with_inputs(torch, pm, n, 5)
     rng = np.random.default_rng(6)

@@ -361,8 +361,7 @@ template <class T, int N> size_t row_fast_smem()
 
 template <class T, int N, int DIR, bool ZP, int V>
 __global__ void __launch_bounds__(Lines<T, N, ZP, V>::TLC * Lines<T, N, ZP, V>::col, Lines<T, N, ZP, V>::col_min_blocks)
-k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg, int64_t stride_j,
-           int64_t ncols, int64_t stride_b, int64_t nlines)
+k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__restrict__ twg)
 {
     using C = typename Cplx<T>::type;
     constexpr int CP = Lines<T, N, ZP, V>::CP;
@@ -372,20 +371,26 @@ k_col_fast(const __grid_constant__ Ptrs ptrs, const typename Cplx<T>::type *__re
     C *tw = reinterpret_cast<C *>(smem);
     C *buf = tw + G::TWN;
     for (int i = threadIdx.x; i < G::TWN; i += blockDim.x) tw[i] = twg[i];
+    // strides and line counts are compile-time constants of N and the pass, so every point's address is the
+    // thread's base plus an immediate (no per-point address registers, no spills)
+    constexpr int H = N / 2 + 1;
+    constexpr int SJ = ZP ? N * H : H;          // point stride
+    constexpr int NLINES = N * H;               // lines (kz, kx) or (ky, kx)
     const int l = threadIdx.x % L, t = threadIdx.x / L;
-    const int64_t g = (int64_t)blockIdx.x * L + l;
-    const bool ok = g < nlines;
-    const int64_t base = ok ? (g / ncols) * stride_b + (g % ncols) : 0;
-    C *data = reinterpret_cast<C *>(ptrs.p[blockIdx.y]);
+    const int g = (int)blockIdx.x * L + l;
+    const bool ok = g < NLINES;
+    // y: line (kz, kx) starts at kz N H + kx; z: line (ky, kx) at ky H + kx = g
+    const int base = ok ? (ZP ? g : (g / H) * (N * H) + g % H) : 0;
+    C *data = reinterpret_cast<C *>(ptrs.p[blockIdx.y]) + base + (int64_t)t * SJ;
     C v[G::P];
 #pragma unroll
     for (int i = 0; i < G::P; i++)
-        v[i] = ok ? data[base + (int64_t)fftc::in_pos<N, CP>(t, i) * stride_j] : fftc::mk<C>(0, 0);
+        v[i] = ok ? data[(int64_t)fftc::in_pos<N, CP>(0, i) * SJ] : fftc::mk<C>(0, 0);
     __syncthreads();
     fftc::fft<C, N, DIR, CP>(v, t, buf, tw, fftc::ColIdx{L, l});
     if (ok) {
 #pragma unroll
-        for (int i = 0; i < G::P; i++) data[base + (int64_t)fftc::out_pos<N, CP>(t, i) * stride_j] = v[i];
+        for (int i = 0; i < G::P; i++) data[(int64_t)fftc::out_pos<N, CP>(0, i) * SJ] = v[i];
     }
 }
 
@@ -505,35 +510,32 @@ template <class T, int N> struct FastPasses {
         set(k_col_fast<T, N, 1, true, V>, col_fast_smem<T, N, true, V>());
     }
     template <bool ZP, int V>
-    static void cols_t(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    static void cols_t(Ctx &c, int nf, const Ptrs &p, int dir)
     {
+        constexpr int64_t nl = (int64_t)N * (N / 2 + 1);   // lines of a y or z pass
         constexpr int L = Lines<T, N, ZP, V>::col;
         constexpr int threads = Lines<T, N, ZP, V>::TLC * L;
         dim3 grid((unsigned)((nl + L - 1) / L), nf);
         const auto *tw = reinterpret_cast<const typename Cplx<T>::type *>(c.tw2);
         const size_t sm = col_fast_smem<T, N, ZP, V>();
         if (dir < 0)
-            k_col_fast<T, N, -1, ZP, V><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
+            k_col_fast<T, N, -1, ZP, V><<<grid, threads, sm, c.stream>>>(p, tw);
         else
-            k_col_fast<T, N, 1, ZP, V><<<grid, threads, sm, c.stream>>>(p, tw, sj, nc, sb, nl);
+            k_col_fast<T, N, 1, ZP, V><<<grid, threads, sm, c.stream>>>(p, tw);
         c.launches++;
     }
     template <bool ZP>
-    static void cols_v(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
+    static void cols_v(Ctx &c, int nf, const Ptrs &p, int dir)
     {
         const int v = Lines<T, N>::tuned ? c.col_shape[ZP ? 1 : 0] : 0;
         if constexpr (Lines<T, N>::tuned) {
-            if (v == 1) return cols_t<ZP, 1>(c, nf, p, sj, nc, sb, nl, dir);
-            if (v == 2) return cols_t<ZP, 2>(c, nf, p, sj, nc, sb, nl, dir);
+            if (v == 1) return cols_t<ZP, 1>(c, nf, p, dir);
+            if (v == 2) return cols_t<ZP, 2>(c, nf, p, dir);
         }
-        cols_t<ZP, 0>(c, nf, p, sj, nc, sb, nl, dir);
+        cols_t<ZP, 0>(c, nf, p, dir);
     }
-    // a z pass has no batch stride (its lines are the whole (ky, kx) plane)
-    static void cols(Ctx &c, int nf, const Ptrs &p, int64_t sj, int64_t nc, int64_t sb, int64_t nl, int dir)
-    {
-        if (sb == 0) cols_v<true>(c, nf, p, sj, nc, sb, nl, dir);
-        else cols_v<false>(c, nf, p, sj, nc, sb, nl, dir);
-    }
+    // y pass (ZP false): lines (kz, kx), points a row apart; z pass: lines (ky, kx), points a plane apart
+    template <bool ZP> static void cols(Ctx &c, int nf, const Ptrs &p, int dir) { cols_v<ZP>(c, nf, p, dir); }
     static void rows(Ctx &c, int nf, const Ptrs &pi, const Ptrs &po, int dir)
     {
         constexpr int L = Lines<T, N>::row;
@@ -581,9 +583,9 @@ void fft_forward(Ctx &c, int nf, const void *const *real_in, void *const *spec_o
         F::attrs();
         F::rows(c, nf, pi, po, -1);
         c.mark(EV_FWD_X);
-        F::cols(c, nf, po, h, h, (int64_t)N * h, (int64_t)N * h, -1);
+        F::template cols<false>(c, nf, po, -1);
         c.mark(EV_FWD_Y);
-        F::cols(c, nf, po, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, -1);
+        F::template cols<true>(c, nf, po, -1);
         c.mark(EV_FWD_Z);
     };
     if (with_fast_n(N, fast)) return;
@@ -617,9 +619,9 @@ void fft_inverse(Ctx &c, int nf, void *const *spec_in, void *const *real_out)
     auto fast = [&]<int NN>() {
         using F = FastPasses<T, NN>;
         F::attrs();
-        F::cols(c, nf, pi, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, +1);
+        F::template cols<true>(c, nf, pi, +1);
         c.mark(EV_INV_Z);
-        F::cols(c, nf, pi, h, h, (int64_t)N * h, (int64_t)N * h, +1);
+        F::template cols<false>(c, nf, pi, +1);
         c.mark(EV_INV_Y);
         F::rows(c, nf, pi, po, +1);
         c.mark(EV_INV_X);
@@ -652,7 +654,6 @@ template <class T>
 int tune_col_pass(Ctx &c, int pass)
 {
     const int N = c.N;
-    const int64_t h = N / 2 + 1;
     Ptrs p{};
     for (int i = 0; i < 9; i++) p.p[i] = reinterpret_cast<typename Cplx<T>::type *>(c.spec) + (size_t)i * c.nh;
     cudaEvent_t e0, e1;
@@ -666,11 +667,11 @@ int tune_col_pass(Ctx &c, int pass)
             with_fast_n(N, [&]<int NN>() {
                 using F = FastPasses<T, NN>;
                 if (pass == 0) {
-                    F::cols(c, 9, p, h, h, (int64_t)N * h, (int64_t)N * h, -1);
-                    F::cols(c, 5, p, h, h, (int64_t)N * h, (int64_t)N * h, +1);
+                    F::template cols<false>(c, 9, p, -1);
+                    F::template cols<false>(c, 5, p, +1);
                 } else {
-                    F::cols(c, 9, p, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, -1);
-                    F::cols(c, 5, p, (int64_t)N * h, (int64_t)N * h, 0, (int64_t)N * h, +1);
+                    F::template cols<true>(c, 9, p, -1);
+                    F::template cols<true>(c, 5, p, +1);
                 }
             });
         };

@@ -763,12 +763,16 @@ __device__ int block_scan_1024(int x, int *wt, int *total)
 __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const int32_t *cnt, int64_t n, int32_t *bsum)
 {
     __shared__ int wt[33];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    // one 16-byte vector per thread, as in k_scan_down (the same four counts)
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int s = 0;
+    if (base + SCAN_ITEMS <= n) {
+        const int4 q = *reinterpret_cast<const int4 *>(cnt + base);
+        s = q.x + q.y + q.z + q.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; k++) {
-        int64_t i = base + (int64_t)k * SCAN_T + threadIdx.x;
-        if (i < n) s += cnt[i];
+        for (int k = 0; k < SCAN_ITEMS; k++)
+            if (base + k < n) s += cnt[base + k];
     }
     int tot;
     block_scan_1024(s, wt, &tot);

@@ -888,15 +888,14 @@ pm_status pm_put_particles_packed_async(pm_ctx *ctx, const pm_packed_particle *p
     CK(cudaStreamWaitEvent(c.io_up, c.ev_in_free, 0));
     CK(cudaMemcpyAsync(c.in_stage, p, bytes, cudaMemcpyDefault, c.io_up));
     CK(cudaEventRecord(c.ev_in_ready, c.io_up));
-    // then, in stream order with the steps: check and load the records, free the staging buffer, sort
+    // then, in stream order with the steps: check the records and sort them by cell straight into the
+    // particle buffer, which frees the staging buffer
     CK(cudaStreamWaitEvent(c.stream, c.ev_in_ready, 0));
     CK(cudaMemsetAsync(c.count, 0, sizeof(int32_t) * c.nc, c.stream));
-    launch_load_packed(c, reinterpret_cast<const pm_packed_particle *>(c.in_stage), 0, c.np,
-                       reinterpret_cast<int *>(c.dscal + 5));
-    CKL("load_packed");
+    launch_put_packed_sorted(c, reinterpret_cast<const pm_packed_particle *>(c.in_stage),
+                             reinterpret_cast<int *>(c.dscal + 5));
+    CKL("put_packed_sorted");
     CK(cudaEventRecord(c.ev_in_free, c.stream));
-    launch_sort<float>(c);
-    CKL("sort");
     return PM_OK;
 }
 

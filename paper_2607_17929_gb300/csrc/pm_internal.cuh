@@ -208,6 +208,8 @@ template <class T>
 void launch_store_particles_scatter(Ctx &c, double *d_pos, double *d_mom);
 // packed records (mixed form): load into the current buffer with checks; store from the id-ordered buffer
 void launch_load_packed(Ctx &c, const pm_packed_particle *in, int64_t first, int64_t count, int *d_bad);
+// all n_part records from device memory counted, checked and placed in cell order (the particle state)
+void launch_put_packed_sorted(Ctx &c, const pm_packed_particle *in, int *d_bad);
 void launch_store_packed(Ctx &c, pm_packed_particle *out, int64_t first, int64_t count);
 template <class T>
 void launch_density(Ctx &c, void *real_out);

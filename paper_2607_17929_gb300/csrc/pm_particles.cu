@@ -893,6 +893,28 @@ __device__ __forceinline__ void pk_copy(uint4 *dst, const uint4 *src, int bytes,
         reinterpret_cast<uint32_t *>(dst)[w] = reinterpret_cast<const uint32_t *>(src)[w];
 }
 
+// one packed record as the particle it stands for; a record with a cell outside [0, nc), an offset outside
+// [0, 1) or a non-finite momentum is flagged (*bad = 1) and kept at a valid cell and offset
+__device__ __forceinline__ Particle<float> unpack_record(const pm_packed_particle &q, uint32_t id, int64_t nc, int *bad)
+{
+    Particle<float> P;
+    P.cell = q.cell;
+    P.id = id;
+    bool ok = q.cell >= 0 && (int64_t)q.cell < nc;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        P.f[d] = q.f[d];
+        P.u[d] = q.u[d];
+        ok = ok && q.f[d] >= 0.f && q.f[d] < 1.f && isfinite(q.u[d]);
+    }
+    if (!ok) {   // keeps the cell index valid; the caller rejects the input
+        *bad = 1;
+        P.cell = 0;
+        P.f[0] = P.f[1] = P.f[2] = 0.f;
+    }
+    return P;
+}
+
 __global__ void __launch_bounds__(256) k_load_packed(const pm_packed_particle *in, int64_t first, int64_t cnt,
                                                      int64_t nc, Particle<float> *out, int32_t *count, int *bad, int vec)
 {
@@ -903,24 +925,42 @@ __global__ void __launch_bounds__(256) k_load_packed(const pm_packed_particle *i
     __syncthreads();
     const pm_packed_particle *sq = reinterpret_cast<const pm_packed_particle *>(sb);
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        const pm_packed_particle q = sq[j];
-        Particle<float> P;
-        P.cell = q.cell;
-        P.id = (uint32_t)(first + base + j);
-        bool ok = q.cell >= 0 && (int64_t)q.cell < nc;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            P.f[d] = q.f[d];
-            P.u[d] = q.u[d];
-            ok = ok && q.f[d] >= 0.f && q.f[d] < 1.f && isfinite(q.u[d]);
-        }
-        if (!ok) {   // keeps the cell index valid; the caller rejects the input
-            *bad = 1;
-            P.cell = 0;
-            P.f[0] = P.f[1] = P.f[2] = 0.f;
-        }
+        const Particle<float> P = unpack_record(sq[j], (uint32_t)(first + base + j), nc, bad);
         out[first + base + j] = P;
         atomicAdd(&count[P.cell], 1);
+    }
+}
+
+// The two passes of a counting sort straight from packed records in device memory: the histogram (with the
+// record checks), then, after the scan, each record placed at its cell's slot as a particle.  Against loading
+// the records into the particle buffer and sorting that, the particle buffer is written once and not read.
+__global__ void __launch_bounds__(256) k_count_packed(const pm_packed_particle *in, int64_t cnt, int64_t nc,
+                                                      int32_t *count, int *bad, int vec)
+{
+    __shared__ uint4 sb[PK_VEC];
+    const int64_t base = (int64_t)blockIdx.x * PK_P;
+    const int nb = (int)min((int64_t)PK_P, cnt - base);
+    pk_copy(sb, reinterpret_cast<const uint4 *>(in + base), nb * 28, vec);
+    __syncthreads();
+    const pm_packed_particle *sq = reinterpret_cast<const pm_packed_particle *>(sb);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x)
+        atomicAdd(&count[unpack_record(sq[j], 0u, nc, bad).cell], 1);
+}
+
+__global__ void __launch_bounds__(256) k_scatter_packed(const pm_packed_particle *in, int64_t cnt, int64_t nc,
+                                                        const int32_t *start, int32_t *count, Particle<float> *out,
+                                                        int *bad, int vec)
+{
+    __shared__ uint4 sb[PK_VEC];
+    const int64_t base = (int64_t)blockIdx.x * PK_P;
+    const int nb = (int)min((int64_t)PK_P, cnt - base);
+    pk_copy(sb, reinterpret_cast<const uint4 *>(in + base), nb * 28, vec);
+    __syncthreads();
+    const pm_packed_particle *sq = reinterpret_cast<const pm_packed_particle *>(sb);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const Particle<float> P = unpack_record(sq[j], (uint32_t)(base + j), nc, bad);
+        const int r = atomicSub(&count[P.cell], 1) - 1;
+        out[start[P.cell] + r] = P;
     }
 }
 
@@ -1295,6 +1335,19 @@ void launch_load_packed(Ctx &c, const pm_packed_particle *in, int64_t first, int
     k_load_packed<<<nblk(count, PK_P), 256, 0, c.stream>>>(in, first, count, c.nc,
                                                            reinterpret_cast<Particle<float> *>(c.part[c.cur]), c.count,
                                                            d_bad, vec);
+}
+
+void launch_put_packed_sorted(Ctx &c, const pm_packed_particle *in, int *d_bad)
+{
+    const int vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    const unsigned nb = nblk(c.np, PK_P);
+    k_count_packed<<<nb, 256, 0, c.stream>>>(in, c.np, c.nc, c.count, d_bad, vec);
+    launch_scan(c);
+    const int o = 1 - c.cur;
+    k_scatter_packed<<<nb, 256, 0, c.stream>>>(in, c.np, c.nc, c.start, c.count,
+                                               reinterpret_cast<Particle<float> *>(c.part[o]), d_bad, vec);
+    c.launches += 2;
+    c.cur = o;
 }
 
 void launch_store_packed(Ctx &c, pm_packed_particle *out, int64_t first, int64_t count)

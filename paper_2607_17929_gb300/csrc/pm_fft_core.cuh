@@ -227,15 +227,18 @@ __device__ __forceinline__ void fft(C (&v)[Geo<N, PP>::P], int t, C *sm, const C
 // complex lines) consecutive rows and rows 8 apart fall in different bank
 // halves, so both the unit-stride reads and the stride-R first-stage writes
 // of a warp take the minimum two wavefronts.  Row kernels store [line][j]
-// with one pad element every 8.
+// with one pad element every 16 (8-byte complex values: a 16-lane half-warp
+// covers exactly the 32 banks both for unit-stride reads and for the
+// radix-8 stage writes, which with a pad every 8 elements met 2-way
+// conflicts in a third of the row passes' wavefronts).
 struct ColIdx {
     int pitch, l;
     __device__ __forceinline__ int operator()(int j) const { return (j ^ ((j >> 3) & 1)) * pitch + l; }
 };
 template <int N> struct RowIdx {
     int base;
-    __device__ __forceinline__ int operator()(int j) const { return base + j + (j >> 3); }
-    static constexpr int pitch = N + N / 8;
+    __device__ __forceinline__ int operator()(int j) const { return base + j + (j >> 4); }
+    static constexpr int pitch = N + N / 16;
 };
 
 }  // namespace fftc

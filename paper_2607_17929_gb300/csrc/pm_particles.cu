@@ -728,102 +728,132 @@ __global__ void __launch_bounds__(KD_THREADS, sizeof(T) == 4 ? 4 : 1) k_kick_bat
 
 // ---------------------------------------------------------------------------
 // Counting sort by cell: exclusive scan of the per-cell counts, then scatter.
+// The scan takes two passes over the counts.  A scan tile is SCAN_ROUNDS rounds of one 16-byte
+// vector per thread; a round covers 4 * SCAN_T consecutive counts, so each warp load and store is
+// 512 contiguous bytes.  The first pass writes each tile's sum.  The second reads its tile again,
+// adds up the sums of the tiles before it (32 KB at 512^3, read from L2 in 16-byte vectors) and
+// writes the exclusive offsets; the last tile also writes the total.
 // ---------------------------------------------------------------------------
-constexpr int SCAN_T = 1024, SCAN_ITEMS = 4;
-constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
+constexpr int SCAN_T = 1024, SCAN_ROUNDS = 4;
+constexpr int SCAN_TILE = SCAN_T * 4 * SCAN_ROUNDS;
 
-__device__ int block_scan_1024(int x, int *wt, int *total)
+// The four counts at cnt[base .. base + 4), zero past n; base is a multiple of 4 (16-byte aligned).
+__device__ __forceinline__ int4 scan_load4(const int32_t *cnt, int64_t n, int64_t base)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int v = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
+    int4 q = make_int4(0, 0, 0, 0);
+    if (base + 4 <= n) {
+        q = *reinterpret_cast<const int4 *>(cnt + base);
+    } else {
+        if (base < n) q.x = cnt[base];
+        if (base + 1 < n) q.y = cnt[base + 1];
+        if (base + 2 < n) q.z = cnt[base + 2];
     }
-    if (lane == 31) wt[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int w = wt[lane], z = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, z, o);
-            if (lane >= o) z += y;
-        }
-        wt[lane] = z - w;
-        if (lane == 31) wt[32] = z;
-    }
-    __syncthreads();
-    int r = wt[wid] + v - x;
-    *total = wt[32];
-    __syncthreads();
-    return r;
+    return q;
 }
 
 __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const int32_t *cnt, int64_t n, int32_t *bsum)
 {
-    __shared__ int wt[33];
-    // one 16-byte vector per thread, as in k_scan_down (the same four counts)
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    int s = 0;
-    if (base + SCAN_ITEMS <= n) {
-        const int4 q = *reinterpret_cast<const int4 *>(cnt + base);
-        s = q.x + q.y + q.z + q.w;
-    } else {
+    __shared__ int wsum[SCAN_T / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * SCAN_TILE + 4 * (int64_t)threadIdx.x;
+    int4 q[SCAN_ROUNDS];
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++)
-            if (base + k < n) s += cnt[base + k];
+    for (int r = 0; r < SCAN_ROUNDS; r++) q[r] = scan_load4(cnt, n, t0 + (int64_t)r * 4 * SCAN_T);
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_ROUNDS; r++) s += q[r].x + q[r].y + q[r].z + q[r].w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) wsum[wid] = s;
+    __syncthreads();
+    if (wid == 0) {
+        int t = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) bsum[blockIdx.x] = t;
     }
-    int tot;
-    block_scan_1024(s, wt, &tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(SCAN_T) k_scan_top(int32_t *bsum, int64_t nb, int32_t *start_end)
-{
-    __shared__ int wt[33];
-    int carry = 0;
-    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_T) {
-        int64_t i = b0 + threadIdx.x;
-        int x = i < nb ? bsum[i] : 0;
-        int tot;
-        int e = block_scan_1024(x, wt, &tot);
-        if (i < nb) bsum[i] = carry + e;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) *start_end = carry;
-}
-
-__global__ void __launch_bounds__(SCAN_T) k_scan_down(const int32_t *cnt, int64_t n, const int32_t *bsum,
+__global__ void __launch_bounds__(SCAN_T, 2) k_scan_down(const int32_t *cnt, int64_t n, const int32_t *bsum,
                                                        int32_t *start)
 {
-    __shared__ int wt[33];
-    static_assert(SCAN_ITEMS == 4, "one 16-byte vector per thread");
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    const bool whole = base + SCAN_ITEMS <= n;   // 16-byte aligned: base is a multiple of 4 ints
-    int v[SCAN_ITEMS], s = 0;
-    if (whole) {
-        const int4 q = *reinterpret_cast<const int4 *>(cnt + base);
-        v[0] = q.x;
-        v[1] = q.y;
-        v[2] = q.z;
-        v[3] = q.w;
-    } else {
+    static_assert(SCAN_T == 1024, "32 warps: one lane of warp 0 per warp");
+    __shared__ int wex[SCAN_ROUNDS][SCAN_T / 32];   // exclusive offset of each warp in each round
+    __shared__ int wpre[SCAN_T / 32];
+    __shared__ int tile_end;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tile = (int)blockIdx.x;
+    const int64_t t0 = (int64_t)tile * SCAN_TILE + 4 * (int64_t)threadIdx.x;
+    int v[SCAN_ROUNDS], inc[SCAN_ROUNDS];
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++) v[k] = base + k < n ? cnt[base + k] : 0;
+    for (int r = 0; r < SCAN_ROUNDS; r++) {
+        const int4 q = scan_load4(cnt, n, t0 + (int64_t)r * 4 * SCAN_T);
+        inc[r] = v[r] = q.x + q.y + q.z + q.w;
     }
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; k++) s += v[k];
-    int tot;
-    const int e = block_scan_1024(s, wt, &tot) + bsum[blockIdx.x];
-    const int o[SCAN_ITEMS] = {e, e + v[0], e + v[0] + v[1], e + v[0] + v[1] + v[2]};
-    if (whole) {
-        *reinterpret_cast<int4 *>(start + base) = make_int4(o[0], o[1], o[2], o[3]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; k++)
-            if (base + k < n) start[base + k] = o[k];
+    // this thread's share of the sums of tiles 0 .. tile-1
+    int pre = 0;
+    const int nv = tile >> 2;
+    for (int i = (int)threadIdx.x; i < nv; i += SCAN_T) {
+        const int4 b = reinterpret_cast<const int4 *>(bsum)[i];
+        pre += b.x + b.y + b.z + b.w;
     }
+    if ((int)threadIdx.x < (tile & 3)) pre += bsum[4 * nv + (int)threadIdx.x];
+    // inclusive warp scans of the thread sums of every round, and the warp sum of pre
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int r = 0; r < SCAN_ROUNDS; r++) {
+            const int y = __shfl_up_sync(0xffffffffu, inc[r], o);
+            if (lane >= o) inc[r] += y;
+        }
+        pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int r = 0; r < SCAN_ROUNDS; r++) wex[r][wid] = inc[r];
+    }
+    if (lane == 0) wpre[wid] = pre;
+    __syncthreads();
+    if (wid == 0) {
+        int w[SCAN_ROUNDS], z[SCAN_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < SCAN_ROUNDS; r++) z[r] = w[r] = wex[r][lane];
+        int p = wpre[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int r = 0; r < SCAN_ROUNDS; r++) {
+                const int y = __shfl_up_sync(0xffffffffu, z[r], o);
+                if (lane >= o) z[r] += y;
+            }
+            p += __shfl_xor_sync(0xffffffffu, p, o);
+        }
+        // round r starts after the tiles before this one and after rounds 0 .. r-1 of this tile
+        int carry = p;
+#pragma unroll
+        for (int r = 0; r < SCAN_ROUNDS; r++) {
+            wex[r][lane] = carry + z[r] - w[r];
+            carry += __shfl_sync(0xffffffffu, z[r], 31);
+        }
+        if (lane == 0) tile_end = carry;
+    }
+    __syncthreads();
+    // the counts again (from L1: this CTA read them above), to keep two CTAs of registers per SM
+#pragma unroll
+    for (int r = 0; r < SCAN_ROUNDS; r++) {
+        const int64_t base = t0 + (int64_t)r * 4 * SCAN_T;
+        const int4 q = scan_load4(cnt, n, base);
+        const int e = wex[r][wid] + inc[r] - v[r];
+        const int4 o = make_int4(e, e + q.x, e + q.x + q.y, e + q.x + q.y + q.z);
+        if (base + 4 <= n) {
+            *reinterpret_cast<int4 *>(start + base) = o;
+        } else {
+            if (base < n) start[base] = o.x;
+            if (base + 1 < n) start[base + 1] = o.y;
+            if (base + 2 < n) start[base + 2] = o.z;
+        }
+    }
+    if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) start[n] = tile_end;
 }
 
 template <class T>
@@ -1284,9 +1314,8 @@ void launch_scan(Ctx &c)
 {
     const int64_t nb = (c.nc + SCAN_TILE - 1) / SCAN_TILE;
     k_scan_reduce<<<(unsigned)nb, SCAN_T, 0, c.stream>>>(c.count, c.nc, c.blocksum);
-    k_scan_top<<<1, SCAN_T, 0, c.stream>>>(c.blocksum, nb, c.start + c.nc);
     k_scan_down<<<(unsigned)nb, SCAN_T, 0, c.stream>>>(c.count, c.nc, c.blocksum, c.start);
-    c.launches += 3;
+    c.launches += 2;
 }
 
 template <class T>

@@ -108,7 +108,7 @@ struct Ctx {
     int cur = 0;
     int32_t *count = nullptr;   // nc
     int32_t *start = nullptr;   // nc + 1
-    int32_t *blocksum = nullptr;
+    int32_t *blocksum = nullptr;   // scan tile sums: one int per 4096 counts, more than the scan's tiles need
     int64_t nblocksum = 0;
     void *phi[3] = {nullptr, nullptr, nullptr};  // ring: phi_{n-2}, phi_{n-1}, phi_n
     int iphi_prev2 = 0, iphi_prev = 1, iphi_new = 2;

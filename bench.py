@@ -666,6 +666,8 @@ def run_reference(args):
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": dict(workload_config(n, box, args.warmup, args.steps, args.gpus),
+                       precision="FP64 throughout (the oracle's plain C loops and FFT)",
+                       l2="host run, no GPU", parallelism=f"OpenMP, {cores} host threads",
                        sampled_from=f"the {args.n}^3 mesh / {args.n}^3 particle benchmark workload"),
         "cpu_baseline": {"value": value, "unit": "particle-updates/s", "cores": cores, "kind": "oracle",
                          "sample": sample + f"; the FP64 CPU oracle on {cores} threads", "host": host_cpu()},

@@ -676,7 +676,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -698,9 +698,21 @@ def main():
     ap.add_argument("--no-config2", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=5)
     ap.add_argument("--ensemble-steps", type=int, default=10)
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.e2e_async_steps is None:
         args.e2e_async_steps = args.steps
+    return args
+
+
+def schedule_length(args):
+    """Steps of the z = 100 -> 0 schedule: the 100 of the benchmark configuration, longer only when the
+    requested warm-up, timed and end-to-end steps of one context do not fit in it."""
+    used = args.warmup + args.steps + 2 * (args.e2e_steps + 1) + (args.e2e_async_steps + 1) + 2
+    return max(N_STEPS_SCHEDULE, used)
+
+
+def main():
+    args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
 
@@ -731,9 +743,7 @@ def main():
     def max_ranks(x):
         return max_over_ranks(x, dist, "cuda")
 
-    # the z = 100 -> 0 schedule of 100 steps, longer only when the requested steps do not fit in it
-    n_sched = max(N_STEPS_SCHEDULE,
-                  args.warmup + args.steps + 2 * (args.e2e_steps + 1) + (args.e2e_async_steps + 1) + 2)
+    n_sched = schedule_length(args)
     # inputs: the same seeded initial conditions for every rank's replica (seed offset per rank)
     probe = pm.PM(8, 8, box, OM, ZI, 0.0, n_sched, pm.PM_MIXED)
     a_n, dtau, _ = probe.schedule()

@@ -1,5 +1,6 @@
 """The measurement code of bench.py on CPU: the compulsory-byte model behind the roofline figures,
-the source check that voids a stale ncu traffic figure, and the parsing of the clock samples."""
+the source check that voids a stale ncu traffic figure, the parsing of the clock samples, and the
+defaults of a run (the schedule length and the end-to-end loop lengths)."""
 import hashlib
 import os
 import sys
@@ -69,3 +70,16 @@ def test_clock_summary_without_samples_says_so(tmp_path):
     c.path = str(tmp_path / "missing.csv")
     s = c.summary()
     assert s["samples"] == 0 and s["sm_mhz"] is None
+
+
+def test_default_run_keeps_the_100_step_schedule_and_times_e2e_over_the_timed_steps():
+    """The default run steps the benchmark's own z = 100 -> 0 schedule of 100 steps, and its overlapped
+    end-to-end loop runs as many steps as the device-timed region."""
+    a = bench.parse_args([])
+    assert (a.n, a.steps, a.warmup) == (512, 30, 5)
+    assert a.e2e_async_steps == a.steps and a.e2e_steps == 10
+    assert bench.schedule_length(a) == bench.N_STEPS_SCHEDULE == 100
+    # the profiling commands (one overlapped step) and a long loop that no longer fits
+    assert bench.parse_args(["--steps", "5", "--e2e-steps", "1", "--e2e-async-steps", "1"]).e2e_async_steps == 1
+    long = bench.parse_args(["--e2e-async-steps", "80"])
+    assert bench.schedule_length(long) == 5 + 30 + 2 * 11 + 81 + 2
